@@ -1,0 +1,212 @@
+"""Seeded synthetic sparse matrices and vectors (CSR, numpy).
+
+This module only generates inputs.  It holds none of the SELL-C-sigma
+arithmetic, so both the CUDA library's tests and the CPU oracle can be fed from
+it without sharing any of the method's code.
+
+The matrices stand in for the University of Florida collection used by the
+paper (Sec. 2.2, Table "table:matrices"), which is not available here:
+
+* ``laplace2d``   5-point Laplacian on an nx x ny grid (diagonal 4, neighbours -1).
+* ``stencil27``   27-point stencil on an n^3 grid (diagonal 26, neighbours -1,
+                  optionally perturbed by a seeded factor 1 + p*U(-1,1) so that
+                  rounding to binary32/bfloat16 is not exact).
+* ``lognormal``   random square matrix; row lengths lognormal with the given mean
+                  and log-standard deviation, rounded to nearest and clamped to
+                  [1, cap]; distinct uniform columns per row, sorted; values N(0,1).
+* ``banded``      random banded matrix: each row has U{lo..hi} distinct columns
+                  within +-bandwidth of the diagonal; values N(0,1).
+* ``beta_worst``  the worst case of Sec. 3.4 (Eq. "betaworst"): one full row and
+                  C-1 single-entry rows in every chunk of C rows.
+* ``random_csr``  small random matrix with a given density (empty rows allowed).
+* ``dense``       a dense n x m matrix stored as CSR.
+* ``long_row``    short rows plus one very long row (a webbase-1M-like profile).
+
+All randomness comes from ``numpy.random.default_rng(seed)``.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+
+@dataclass
+class CSR:
+    nrows: int
+    ncols: int
+    rpt: np.ndarray  # int64[nrows + 1]
+    col: np.ndarray  # int32[nnz], ascending inside each row
+    val: np.ndarray  # float64[nnz]
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rpt[-1]) if self.nrows > 0 else 0
+
+    def row_lengths(self) -> np.ndarray:
+        return np.diff(self.rpt)
+
+    def to_dense(self) -> np.ndarray:
+        d = np.zeros((self.nrows, self.ncols), np.float64)
+        rows = np.repeat(np.arange(self.nrows), self.row_lengths())
+        d[rows, self.col.astype(np.int64)] = self.val
+        return d
+
+
+def _from_lengths(rl: np.ndarray, ncols: int, col: np.ndarray, val: np.ndarray) -> CSR:
+    rpt = np.zeros(rl.shape[0] + 1, np.int64)
+    np.cumsum(rl, out=rpt[1:])
+    return CSR(int(rl.shape[0]), int(ncols), rpt, np.ascontiguousarray(col, np.int32),
+               np.ascontiguousarray(val, np.float64))
+
+
+def laplace2d(nx: int, ny: int | None = None) -> CSR:
+    ny = nx if ny is None else ny
+    n = nx * ny
+    idx = np.arange(n, dtype=np.int64)
+    gx, gy = idx % nx, idx // nx
+    # neighbours in ascending column order: (y-1), (x-1), self, (x+1), (y+1)
+    offs = [(-nx, gy > 0, -1.0), (-1, gx > 0, -1.0), (0, np.ones(n, bool), 4.0),
+            (1, gx < nx - 1, -1.0), (nx, gy < ny - 1, -1.0)]
+    cols = np.stack([idx + o for o, _, _ in offs], axis=1)
+    mask = np.stack([m for _, m, _ in offs], axis=1)
+    vals = np.broadcast_to(np.array([v for _, _, v in offs]), cols.shape)
+    return _from_lengths(mask.sum(1), n, cols[mask], vals[mask])
+
+
+def stencil27(n: int, perturb: float = 0.0, seed: int = 0) -> CSR:
+    N = n ** 3
+    idx = np.arange(N, dtype=np.int64)
+    gx, gy, gz = idx % n, (idx // n) % n, idx // (n * n)
+    cols = np.empty((N, 27), np.int32)
+    mask = np.empty((N, 27), bool)
+    vals = np.empty((N, 27), np.float64)
+    t = 0
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                ok = ((gx + dx >= 0) & (gx + dx < n) & (gy + dy >= 0) & (gy + dy < n)
+                      & (gz + dz >= 0) & (gz + dz < n))
+                cols[:, t] = idx + dz * n * n + dy * n + dx
+                mask[:, t] = ok
+                vals[:, t] = 26.0 if (dx, dy, dz) == (0, 0, 0) else -1.0
+                t += 1
+    rl = mask.sum(1)
+    col = cols[mask]
+    del cols
+    val = vals[mask]
+    del vals, mask
+    if perturb:
+        rng = np.random.default_rng(seed)
+        val *= 1.0 + perturb * rng.uniform(-1.0, 1.0, val.shape[0])
+    return _from_lengths(rl, N, col, val)
+
+
+def lognormal_lengths(N: int, mean: float = 16.0, sigma_ln: float = 1.2, cap: int = 2000,
+                      rng=None) -> np.ndarray:
+    """Row lengths whose underlying normal has mu = ln(mean) - sigma_ln^2/2, so
+    that the unclamped mean is ``mean``; rounded to nearest, clamped to [1, cap]."""
+    rng = np.random.default_rng(0) if rng is None else rng
+    mu = np.log(mean) - 0.5 * sigma_ln * sigma_ln
+    rl = np.rint(np.exp(mu + sigma_ln * rng.standard_normal(N)))
+    return np.clip(rl, 1, cap).astype(np.int64)
+
+
+def _distinct_sorted_columns(rl: np.ndarray, lo: np.ndarray, hi: np.ndarray, rng) -> np.ndarray:
+    """For every row i draw rl[i] distinct integers uniformly from [lo[i], hi[i]),
+    sorted ascending; rows are concatenated in row order."""
+    N = rl.shape[0]
+    rows = np.repeat(np.arange(N, dtype=np.int64), rl)
+    span = (hi - lo)[rows]
+    base = lo[rows]
+    width = int(max(1, (hi - lo).max(initial=1)))
+    cols = base + rng.integers(0, np.iinfo(np.int64).max, rows.shape[0]) % span
+    while True:
+        key = rows * width + (cols - base)
+        order = np.argsort(key, kind="stable")
+        ks = key[order]
+        dup = np.nonzero(ks[1:] == ks[:-1])[0] + 1
+        if dup.size == 0:
+            return cols[order]
+        at = order[dup]
+        cols[at] = base[at] + rng.integers(0, np.iinfo(np.int64).max, at.shape[0]) % span[at]
+
+
+def lognormal(N: int, mean: float = 16.0, sigma_ln: float = 1.2, cap: int = 2000,
+              seed: int = 0) -> CSR:
+    rng = np.random.default_rng(seed)
+    cap = min(cap, N)
+    rl = lognormal_lengths(N, mean, sigma_ln, cap, rng)
+    col = _distinct_sorted_columns(rl, np.zeros(N, np.int64), np.full(N, N, np.int64), rng)
+    val = rng.standard_normal(col.shape[0])
+    return _from_lengths(rl, N, col, val)
+
+
+def banded(N: int, bandwidth: int = 64, lo: int = 7, hi: int = 30, seed: int = 0) -> CSR:
+    rng = np.random.default_rng(seed)
+    i = np.arange(N, dtype=np.int64)
+    a = np.maximum(i - bandwidth, 0)
+    b = np.minimum(i + bandwidth + 1, N)
+    rl = np.minimum(rng.integers(lo, hi + 1, N), b - a)
+    col = _distinct_sorted_columns(rl, a, b, rng)
+    val = rng.standard_normal(col.shape[0])
+    return _from_lengths(rl, N, col, val)
+
+
+def beta_worst(N: int, C: int, seed: int = 0) -> CSR:
+    """Sec. 3.4 worst case: in every chunk of C rows the first row is full
+    (N entries) and the other C-1 rows hold one entry (on the diagonal)."""
+    assert N % C == 0
+    rng = np.random.default_rng(seed)
+    rl = np.ones(N, np.int64)
+    rl[::C] = N
+    cols = []
+    for i in range(N):
+        cols.append(np.arange(N) if i % C == 0 else np.array([i]))
+    col = np.concatenate(cols)
+    val = rng.uniform(-1.0, 1.0, col.shape[0])
+    return _from_lengths(rl, N, col, val)
+
+
+def random_csr(N: int, M: int | None = None, density: float = 0.1, seed: int = 0,
+               empty_rows: float = 0.0) -> CSR:
+    M = N if M is None else M
+    rng = np.random.default_rng(seed)
+    d = rng.random((N, M)) < density
+    if empty_rows > 0:
+        d[rng.random(N) < empty_rows, :] = False
+    rows, cols = np.nonzero(d)
+    val = rng.standard_normal(rows.shape[0])
+    return _from_lengths(d.sum(1), M, cols, val)
+
+
+def dense(N: int, M: int | None = None, seed: int = 0) -> CSR:
+    M = N if M is None else M
+    rng = np.random.default_rng(seed)
+    rl = np.full(N, M, np.int64)
+    col = np.tile(np.arange(M, dtype=np.int32), N)
+    val = rng.standard_normal(N * M)
+    return _from_lengths(rl, M, col, val)
+
+
+def long_row(N: int, long_len: int, short_len: int = 3, at: int = 0, seed: int = 0) -> CSR:
+    rng = np.random.default_rng(seed)
+    rl = np.full(N, min(short_len, N), np.int64)
+    rl[at] = min(long_len, N)
+    col = _distinct_sorted_columns(rl, np.zeros(N, np.int64), np.full(N, N, np.int64), rng)
+    val = rng.standard_normal(col.shape[0])
+    return _from_lengths(rl, N, col, val)
+
+
+def from_dense(d: np.ndarray) -> CSR:
+    rows, cols = np.nonzero(d)
+    return _from_lengths((d != 0).sum(1), d.shape[1], cols, d[rows, cols])
+
+
+def vector(n: int, seed: int = 0, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
+    return np.random.default_rng(seed).uniform(lo, hi, n)
+
+
+def block(n: int, k: int, seed: int = 0) -> np.ndarray:
+    """Row-major n x k block of right-hand sides, U[-1, 1]."""
+    return np.random.default_rng(seed).uniform(-1.0, 1.0, (n, k))
