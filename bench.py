@@ -1,0 +1,487 @@
+#!/usr/bin/env python
+"""SELL-C-sigma SpMV benchmark (GB300, sm_103a).
+
+Default workload: random square matrix, N = 2,000,000 rows, row lengths
+lognormal (mean 16, log-sd 1.2, capped at 2000), uniform distinct columns,
+N(0,1) binary64 values, x ~ U[-1, 1] (seed 0).  The format is built once for
+every point of the sweep C in {32, 64, 128} x sigma in {1, 256, 4096, N};
+the headline step is one binary64 SpMV y = A x at the fastest point.
+
+One JSON line is printed by rank 0.  Under torchrun every rank runs its own
+replica of the workload on its own GPU (independent problems, no data-path
+collective: weak scaling); the step time is the maximum over ranks.
+
+--impl reference runs the CPU oracle (CRS SpMV in binary64, OpenMP on the
+host cores) on a bounded row sample per step instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+L2_BYTES = 129 * 2 ** 20
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_SOURCES = ["paper_1307_6209_gb300/csrc/sell_spmv.cu", "paper_1307_6209_gb300/csrc/sell_internal.cuh"]
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10000)
+    p.add_argument("--warmup", type=int, default=100)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", choices=["lognormal", "stencil27", "laplace"], default="lognormal")
+    p.add_argument("--n", type=int, default=None, help="rows (lognormal) or grid edge (stencils)")
+    p.add_argument("--C", type=int, default=None)
+    p.add_argument("--sigma", type=int, default=None)
+    p.add_argument("--no-sweep", action="store_true")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--no-extras", action="store_true", help="skip SpMMV / mixed / e2e extras")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ workload
+def make_workload(args):
+    from paper_1307_6209_gb300 import synth
+    if args.workload == "lognormal":
+        n = args.n or 2_000_000
+        A = synth.lognormal(n, mean=16.0, sigma_ln=1.2, cap=2000, seed=0)
+        desc = f"lognormal random N={n} (row length mean 16, log-sd 1.2, cap 2000), FP64"
+        grid = [(C, s) for C in (32, 64, 128) for s in (1, 256, 4096, n)]
+    elif args.workload == "stencil27":
+        n = args.n or 200
+        A = synth.stencil27(n, perturb=0.1, seed=0)
+        desc = f"27-point stencil on a {n}^3 grid, FP64"
+        grid = [(32, 1), (32, 4096), (64, 1), (128, 1)]
+    else:
+        n = args.n or 64
+        A = synth.laplace2d(n)
+        desc = f"5-point Laplacian on a {n}x{n} grid, FP64"
+        grid = [(32, 1)]
+    x = synth.vector(A.ncols, seed=0)
+    return A, x, desc, grid
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def lookup_traffic(workload_key):
+    """dram bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None, None
+    e = d.get(workload_key)
+    if not e or e.get("src_sha") != kernel_source_hash():
+        return None, None
+    return e.get("dram_bytes_per_launch"), e.get("note")
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.samples.append((time.time(), [v.strip() for v in ln.split(",")]))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        win = [s for t, s in self.samples if t0 - 0.25 <= t <= t1 + 0.25]
+        if not win and self.samples:
+            mid = 0.5 * (t0 + t1)
+            win = [min(self.samples, key=lambda ts: abs(ts[0] - mid))[1]]
+        if not win:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(s[1]) for s in win if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in win if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in win:
+            for i, nm in enumerate(names):
+                if len(s) > 5 + i and s[5 + i].lower().startswith("active"):
+                    reasons.add(nm)
+        pw = [float(s[3]) for s in win if s[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(win),
+                "power_w_median": statistics.median(pw) if pw else None}
+
+
+# ------------------------------------------------------------------ helpers
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def time_spmv(sell, h, xd, yd, stream, reps, warm=3, flags=0):
+    import torch
+    for _ in range(warm):
+        sell.sell_spmv(h, xd, yd, flags=flags, stream=stream)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        sell.sell_spmv(h, xd, yd, flags=flags, stream=stream)
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) / reps * 1e-3
+
+
+def time_spmmv(sell, h, Xd, Yd, stream, reps, warm=3, flags=0):
+    import torch
+    for _ in range(warm):
+        sell.sell_spmmv(h, Xd, Yd, flags=flags, stream=stream)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        sell.sell_spmmv(h, Xd, Yd, flags=flags, stream=stream)
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) / reps * 1e-3
+
+
+def measure_read_bw(sell, stream, nbytes=4 * 2 ** 30, reps=10):
+    import torch
+    buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    buf.fill_(1)
+    sink = torch.empty(152 * 8, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        sell.sell_bench_read(buf, nbytes, sink, grid=152 * 4, stream=stream)
+    best = 1e30
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sell.sell_bench_read(buf, nbytes, sink, grid=152 * 4, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        best = min(best, a.elapsed_time(b) * 1e-3)
+    del buf
+    return nbytes / best / 1e9
+
+
+def measure_fp64_fma(sell, stream, iters=2000):
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    grid = sms * 8
+    sink = torch.empty(grid * 256, dtype=torch.float64, device="cuda")
+    sell.sell_bench_fma64(sink, grid, 10, stream=stream)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    sell.sell_bench_fma64(sink, grid, iters, stream=stream)
+    b.record(stream)
+    b.synchronize()
+    fmas = grid * 256 * iters * 64
+    return 2.0 * fmas / (a.elapsed_time(b) * 1e-3) / 1e12
+
+
+def cpu_baseline(A, x, target_s=10.0):
+    """The oracle's CRS SpMV (binary64, OpenMP on all host cores, STATIC or
+    GUIDED,1 by the zeta heuristic of Sec. 5) timed on the full matrix."""
+    import oracle
+    nth = os.cpu_count() or 1
+    zeta = oracle.zeta(A.row_lengths().astype(np.int32))
+    guided = zeta >= 0.4
+    t0 = time.perf_counter()
+    oracle.csr_spmv(A, x, nthreads=nth, guided=guided)
+    one = time.perf_counter() - t0
+    reps = max(1, int(target_s / max(one, 1e-6)))
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.csr_spmv(A, x, nthreads=nth, guided=guided)
+    dt = (time.perf_counter() - t0) / reps
+    return {"value": round(2.0 * A.nnz / dt / 1e9, 3), "unit": "GF/s", "cores": nth, "kind": "oracle",
+            "sample": f"full matrix ({A.nnz} nnz), {reps} calls, schedule "
+                      f"{'GUIDED,1' if guided else 'STATIC'} (zeta={zeta:.2f})"}
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1307_6209_gb300 import synth
+    A, x, desc, _ = make_workload(args)
+    nth = os.cpu_count() or 1
+    zeta = oracle.zeta(A.row_lengths().astype(np.int32))
+    guided = zeta >= 0.4
+    t0 = time.perf_counter()
+    oracle.csr_spmv(A, x, nthreads=nth, guided=guided)
+    t_full = time.perf_counter() - t0
+    budget = 90.0  # seconds for warm-up + timed steps
+    frac = min(1.0, budget / max((args.steps + args.warmup) * t_full, 1e-9))
+    nrow = max(1, int(A.nrows * frac))
+    S = synth.CSR(nrow, A.ncols, A.rpt[:nrow + 1].copy(), A.col[:A.rpt[nrow]], A.val[:A.rpt[nrow]])
+    for _ in range(args.warmup):
+        oracle.csr_spmv(S, x, nthreads=nth, guided=guided)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.csr_spmv(S, x, nthreads=nth, guided=guided)
+    dt = time.perf_counter() - t0
+    gf = 2.0 * S.nnz * args.steps / dt / 1e9
+    sample = (f"rows 0..{nrow - 1} of the workload ({S.nnz} nnz, {100 * frac:.2f}% of it) per step, "
+              f"binary64 CRS SpMV, OpenMP {'GUIDED,1' if guided else 'STATIC'}")
+    line = {"impl": "reference", "metric": "SpMV GF/s", "value": round(gf, 3), "unit": "GF/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "sample": sample},
+            "cpu_baseline": {"value": round(gf, 3), "unit": "GF/s", "cores": nth, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(gf, 3), "unit": "GF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+    from paper_1307_6209_gb300 import build as cuda_build
+    from paper_1307_6209_gb300 import model, sell
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    cuda_build.build()
+    sell.load()
+    stream = torch.cuda.Stream()
+    A, x, desc, grid = make_workload(args)
+    n_gpus = ws
+    dev_name = torch.cuda.get_device_name(local)
+
+    with torch.cuda.stream(stream):
+        xd = torch.from_numpy(x).cuda()
+        yd = torch.empty(A.nrows, dtype=torch.float64, device="cuda")
+        csr_d = type(A)(A.nrows, A.ncols, torch.from_numpy(A.rpt).cuda(), torch.from_numpy(A.col).cuda(),
+                        torch.from_numpy(A.val).cuda())
+        torch.cuda.synchronize()
+
+        # ---- sweep of (C, sigma): build once each, time 50 SpMVs
+        sweep = []
+        if args.C is not None or args.sigma is not None or args.no_sweep:
+            grid = [(args.C or 32, args.sigma or 1)]
+        best = None
+        for C, sigma in grid:
+            t0 = time.perf_counter()
+            h = sell.sell_build(csr_d, C=C, sigma=sigma, stream=stream)
+            build_ms = (time.perf_counter() - t0) * 1e3
+            dt = time_spmv(sell, h, xd, yd, stream, reps=50)
+            gf = 2.0 * A.nnz / dt / 1e9
+            sweep.append({"C": C, "sigma": sigma, "beta": round(h.info.beta, 4), "gflops": round(gf, 1),
+                          "us": round(dt * 1e6, 2), "build_ms": round(build_ms, 2)})
+            if best is None or gf > best[0]:
+                if best is not None:
+                    best[1].free()
+                best = (gf, h, C, sigma, build_ms)
+            else:
+                h.free()
+        _, h, C, sigma, build_ms = best
+        inf = h.info
+
+        # ---- measuring kernels: read bandwidth b (Listing "reduction" analogue), FP64 FMA peak
+        b_read = measure_read_bw(sell, stream) if rank == 0 else None
+        fma_tf = measure_fp64_fma(sell, stream) if rank == 0 else None
+
+        # ---- the timed region: K steps of one SpMV each
+        clk = ClockSampler(local)
+        clk.start()
+        for _ in range(args.warmup):
+            sell.sell_spmv(h, xd, yd, stream=stream)
+        ev_a = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        wall0 = time.time()
+        t_start.record(stream)
+        for i in range(args.steps):
+            ev_a[i].record(stream)
+            sell.sell_spmv(h, xd, yd, stream=stream)
+            ev_b[i].record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        wall1 = time.time()
+        clk.stop()
+        total_s = t_start.elapsed_time(t_end) * 1e-3
+        kern_s = sum(a.elapsed_time(b) for a, b in zip(ev_a, ev_b)) * 1e-3 / args.steps
+        if dist:
+            t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_s = float(t.item())
+        step_s = total_s / args.steps
+        flops = 2.0 * A.nnz
+        value = n_gpus * flops / step_s / 1e9
+
+        extras = {}
+        e2e = None
+        if not args.no_extras:
+            # ---- end to end through the C ABI with host buffers (pinned)
+            xh = torch.from_numpy(x).pin_memory()
+            yh = torch.empty(A.nrows, dtype=torch.float64).pin_memory()
+            ke = min(args.steps, 2000)
+            for _ in range(5):
+                sell.sell_spmv(h, xh, yh, flags=sell.SELL_SPMV_HOST_IO, stream=stream)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(ke):
+                sell.sell_spmv(h, xh, yh, flags=sell.SELL_SPMV_HOST_IO, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            e2e_s = a.elapsed_time(b) * 1e-3 / ke
+            e2e = {"value": round(n_gpus * flops / e2e_s / 1e9, 2), "unit": "GF/s",
+                   "h2d_bytes_per_step": 8 * A.ncols, "d2h_bytes_per_step": 8 * A.nrows}
+
+            # ---- multiple right-hand sides (A streamed once for k vectors)
+            spmmv = {}
+            for k in (4, 8):
+                Xd = torch.from_numpy(np.tile(x[:, None], (1, k))).cuda()
+                Yd = torch.empty((A.nrows, k), dtype=torch.float64, device="cuda")
+                dt = time_spmmv(sell, h, Xd, Yd, stream, reps=50)
+                spmmv[f"k{k}"] = {"gflops": round(2.0 * A.nnz * k / dt / 1e9, 1), "us": round(dt * 1e6, 2)}
+                del Xd, Yd
+            extras["spmmv_f64"] = spmmv
+
+            # ---- reduced-precision storage: binary32 / bfloat16 values, binary32 accumulation
+            mixed = {}
+            y64 = yd.clone()
+            x32 = xd.float()
+            for name, st in (("f32", sell.SELL_F32), ("bf16", sell.SELL_BF16)):
+                hm = sell.sell_build(csr_d, C=C, sigma=sigma, store_type=st, stream=stream)
+                y32 = torch.empty(A.nrows, dtype=torch.float32, device="cuda")
+                row = {}
+                for tag, fl in (("plain", 0), ("dot2", sell.SELL_SPMV_COMPENSATED)):
+                    dt = time_spmv(sell, hm, x32, y32, stream, reps=100, flags=fl)
+                    torch.cuda.synchronize()
+                    err = (y32.double() - y64).abs()
+                    row[tag] = {"gflops": round(flops / dt / 1e9, 1), "us": round(dt * 1e6, 2),
+                                "speedup_vs_f64": round(step_s / dt, 3),
+                                "max_abs_err_vs_f64": float(err.max()),
+                                "rel_err_vs_f64": float(err.norm() / y64.norm())}
+                mixed[name] = row
+                hm.free()
+            extras["mixed"] = mixed
+
+    # ---- roofline of the dominant kernel (the SpMV)
+    peak, peak_src = load_peaks()
+    alg = model.algorithmic_bytes(A.nrows, A.ncols, A.nnz, inf.nchunks, C, 8, 8, inf.has_perm)
+    achieved = alg / kern_s / 1e9
+    wl_key = f"{args.workload}:C{C}:s{sigma}:N{A.nrows}"
+    traffic, _ = lookup_traffic(wl_key)
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic,
+            "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
+            "kernel": "k_spmmv<double,1,U,Plain<double>>", "kernel_avg_us": round(kern_s * 1e6, 3),
+            "algorithmic_bytes_per_launch": alg}
+    pm_bytes = model.paper_model_bytes(A.nnz, inf.beta, A.nrows, A.ncols)
+    nnzr = A.nnz / A.nrows
+    extras["paper_model"] = {
+        "beta": inf.beta, "nnzr": round(nnzr, 3), "zeta": round(inf.zeta, 3),
+        "balance_bytes_per_flop": round(model.balance_sell(1.0 / nnzr, inf.beta, nnzr), 4),
+        "bound_gflops_measured_b": round(model.roofline(b_read or peak, model.balance_sell(1.0 / nnzr, inf.beta, nnzr)), 1),
+        "frac_of_model_bound": round(value / n_gpus / model.roofline(b_read or peak, model.balance_sell(1.0 / nnzr, inf.beta, nnzr)), 4),
+        "model_bytes_per_launch": int(pm_bytes)}
+    extras["b_read_gbs"] = round(b_read, 1) if b_read else None
+    extras["fp64_fma_peak_tflops"] = round(fma_tf, 3) if fma_tf else None
+    extras["fp64_pipe_frac"] = round(flops / kern_s / 1e12 / fma_tf, 4) if fma_tf else None
+    extras["build_ms"] = round(build_ms, 2)
+    extras["sweep"] = sweep
+    extras["device"] = dev_name
+
+    if rank == 0:
+        cb = None
+        if not args.no_cpu and ws == 1:
+            cb = cpu_baseline(A, x)
+        line = {
+            "metric": "SpMV GF/s (FP64, SELL-C-sigma)", "value": round(value, 2), "unit": "GF/s",
+            "n_gpus": n_gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(step_s * 1e3, 5), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "C": C, "sigma": sigma, "nrows": A.nrows, "nnz": A.nnz,
+                       "beta": round(inf.beta, 6), "stored": inf.stored,
+                       "l2": f"inputs larger than L2: the matrix streams {alg / 1e9:.2f} GB per step "
+                             f"(L2 {L2_BYTES / 2 ** 20:.0f} MiB); x stays L2-resident by design",
+                       "parallelism": f"replicas x{n_gpus}"},
+            "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": args.steps,
+            "clocks": clk.summary(wall0, wall1),
+        }
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,254 @@
+/*
+ * sell.h -- C ABI of the SELL-C-sigma library for NVIDIA GB300 (sm_103a).
+ *
+ * The library converts a sparse matrix from CRS (compressed row storage) into
+ * the SELL-C-sigma format of Kreutzer, Hager, Wellein, Fehske and Bishop,
+ * "A unified sparse matrix data format for efficient general sparse
+ * matrix-vector multiply on modern processors with wide SIMD units"
+ * (arXiv:1307.6209, SIAM J. Sci. Comput.), and multiplies it with vectors and
+ * blocks of vectors on the GPU.  Every step runs in the library's own CUDA
+ * kernels.
+ *
+ * Conventions that hold for every call:
+ *   - Every call returns a sell_status; nothing is thrown across the ABI.
+ *     sell_last_error() gives a message for the calling thread's last failure.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  sell_spmv, sell_spmmv and sell_batch_run are asynchronous on
+ *     it.  sell_build synchronises the stream: it reads two sizes back and
+ *     returns once the format is complete on the device;
+ *     sell_export and sell_free synchronise the device.
+ *   - Device pointers belong to the current CUDA device; a handle must be used
+ *     on the device that was current when it was built.
+ *   - Index types: row offsets int64, column indices int32 (Sec. 5: four-byte
+ *     indices), chunk offsets int64.
+ *   - The library allocates its device memory through sell_set_allocator's
+ *     callbacks (default: cudaMallocAsync / cudaFreeAsync on the build stream).
+ */
+#ifndef SELL_H
+#define SELL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SELL_API __attribute__((visibility("default")))
+#else
+#define SELL_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- types */
+
+/* Value types.  The paper stores binary64 only (Sec. 5); binary32 and
+ * bfloat16 storage with binary32 accumulation are this library's extension. */
+enum { SELL_F64 = 0, SELL_F32 = 1, SELL_BF16 = 2 };
+
+typedef enum {
+    SELL_OK = 0,
+    SELL_EINVAL = 1,       /* bad argument or malformed CRS input */
+    SELL_ENOMEM = 2,       /* an allocation failed; nothing leaked */
+    SELL_ECUDA = 3,        /* a CUDA runtime call failed (message kept) */
+    SELL_EBOUNDS = 4,      /* a kernel's own bounds check fired */
+    SELL_ETIMEOUT = 5,     /* a bounded device-side wait gave up */
+    SELL_EUNSUPPORTED = 6  /* valid request this build does not support */
+} sell_status;
+
+/* CRS input (Sec. 3.1, Listing "crs"): row i holds entries rpt[i]..rpt[i+1]-1
+ * of col[] and val[].  The matrix is borrowed for the duration of sell_build
+ * only and never retained.  Requirements (checked, else SELL_EINVAL):
+ * rpt[0] = 0, rpt non-decreasing, rpt[nrows] = nnz, every row length and
+ * nrows below 2^31, 0 <= col[j] < ncols < 2^31.  Explicit zeros are stored
+ * like any other entry.  val_type is SELL_F64 or SELL_F32. */
+typedef struct {
+    int64_t nrows;
+    int64_t ncols;
+    int64_t nnz;
+    const int64_t *rpt;  /* nrows + 1 */
+    const int32_t *col;  /* nnz */
+    const void *val;     /* nnz elements of val_type */
+    int32_t val_type;
+    int32_t on_device;   /* 1: the three arrays are device pointers, 0: host */
+} sell_csr;
+
+/* Build flags. */
+#define SELL_BUILD_PERMUTE_COLS 0x1u  /* renumber columns by the row permutation
+                                         (square matrices only, Sec. 3.4): the
+                                         handle then computes P A P^T and takes
+                                         x, y in sorted-row order */
+
+/* Build parameters (Sec. 3.3-3.4). */
+typedef struct {
+    int32_t C;          /* chunk height, >= 1 (GPU default 32: one warp/chunk) */
+    int32_t store_type; /* SELL_F64, SELL_F32 or SELL_BF16: value storage */
+    int64_t sigma;      /* sorting scope, >= 1; 1 = no sort, >= nrows = global */
+    uint32_t flags;     /* SELL_BUILD_* */
+    int32_t reserved;   /* must be 0 */
+} sell_opts;
+
+typedef struct sell_matrix *sell_handle;
+
+/* What a handle holds (all counts of the built format). */
+typedef struct {
+    int64_t nrows, ncols, nnz;
+    int64_t nchunks;      /* Nc = ceil(nrows / C), Eq. "nc" */
+    int64_t stored;       /* cs[Nc] = sum_c C * cl[c], padding included */
+    int64_t max_row_len;
+    int64_t sigma;
+    int32_t C;
+    int32_t store_type;
+    uint32_t flags;
+    int32_t has_perm;     /* 0 when sigma <= 1 (the permutation is identity) */
+    double beta;          /* Eq. "beta": nnz / stored (1 when stored = 0) */
+    double zeta;          /* Eq. "cv": coefficient of variation of row lengths */
+    size_t device_bytes;  /* device memory owned by the handle */
+} sell_info_t;
+
+/* Device-memory callbacks: alloc(bytes, ctx, stream) returns a device pointer
+ * or NULL; release(ptr, ctx, stream) frees it (may be called with NULL). */
+typedef void *(*sell_alloc_fn)(size_t bytes, void *ctx, void *stream);
+typedef void (*sell_free_fn)(void *ptr, void *ctx, void *stream);
+
+/* ---------------------------------------------------------------- calls */
+
+/* Install process-wide allocation callbacks (both NULL restores the
+ * default).  Handles keep the callbacks they were built with. */
+SELL_API sell_status sell_set_allocator(sell_alloc_fn alloc, sell_free_fn release, void *ctx);
+
+/* Convert CRS into SELL-C-sigma (Sec. 3.3 and 3.4, Eqs. "nc", "max"):
+ *  1. rowLen[i] = rpt[i+1] - rpt[i];
+ *  2. inside each window [w*sigma, min((w+1)*sigma, nrows)) rows are sorted by
+ *     rowLen in descending order, equal lengths keeping their order;
+ *     perm[r] = original row of sorted row r;
+ *  3. chunks of C sorted rows; cl[c] = longest row of chunk c (rows past nrows
+ *     count as empty);
+ *  4. cs[0] = 0, cs[c+1] = cs[c] + C * cl[c];
+ *  5. entry j of sorted row r = c*C + l is stored at cs[c] + j*C + l
+ *     (column-major inside the chunk, Listing "sell"); padding has value 0 and
+ *     column 0 (Sec. 4).  With SELL_BUILD_PERMUTE_COLS the stored column is
+ *     invperm[col].
+ * Values are converted to opts->store_type with one round-to-nearest-even.
+ * On success *out owns all device arrays; release it with sell_free.
+ * Errors: SELL_EINVAL (bad opts or CRS; *out untouched), SELL_ENOMEM,
+ * SELL_ECUDA.  Synchronises `stream` (to read the maximum row length and the
+ * stored size, and before returning), so the handle may be used on any stream
+ * afterwards. */
+SELL_API sell_status sell_build(const sell_csr *A, const sell_opts *opts, void *stream,
+                       sell_handle *out);
+
+/* SpMV flags. */
+#define SELL_SPMV_ACCUMULATE 0x1u   /* y = y + A x instead of y = A x */
+#define SELL_SPMV_COMPENSATED 0x2u  /* F32/BF16 storage: compensated (Dot2)
+                                       binary32 accumulation of each row */
+#define SELL_SPMV_HOST_IO 0x4u      /* x and y (X and Y) are host pointers; the
+                                       copies to and from the handle's staging
+                                       buffers are issued on `stream` */
+
+/* y = A x over the SELL-C-sigma handle (Listing "sell", one GPU thread per
+ * row of a chunk, each thread stopping at its own row length -- Sec. 3.4, the
+ * "Sliced ELLR-T" variant with T = 1).  Each row is summed in CRS order with
+ * fused multiply-adds.
+ * Types: F64 storage -> x, y binary64; F32/BF16 storage -> x, y binary32 with
+ * binary32 accumulation (SELL_SPMV_COMPENSATED: error-free product and sum
+ * transformations, result rounded once).
+ * x has ncols elements and y nrows, both in the original row order unless the
+ * handle was built with SELL_BUILD_PERMUTE_COLS (then both in sorted order).
+ * x and y must not overlap.  Asynchronous on `stream`.
+ * Errors: SELL_EINVAL (NULL handle/pointer), SELL_EUNSUPPORTED (COMPENSATED
+ * on F64 storage), SELL_ENOMEM (HOST_IO staging), SELL_ECUDA. */
+SELL_API sell_status sell_spmv(sell_handle h, const void *x, void *y, uint32_t flags, void *stream);
+
+/* Y = A X for k right-hand sides (not in the paper; the matrix is streamed
+ * once for up to 8 vectors).  X is ncols x k and Y nrows x k, row-major with
+ * leading dimensions ldx >= k and ldy >= k (in elements); element types as in
+ * sell_spmv.  k > 8 is processed in blocks of 8 columns, streaming the
+ * matrix once per block.  Column c of Y equals sell_spmv of column c of X
+ * bit for bit.  Errors as sell_spmv, plus SELL_EINVAL for k < 1, ldx < k,
+ * ldy < k. */
+SELL_API sell_status sell_spmmv(sell_handle h, const void *X, int64_t ldx, void *Y, int64_t ldy,
+                       int32_t k, uint32_t flags, void *stream);
+
+/* Launch tuning of a handle's SpMV/SpMMV kernels (autotuner knob):
+ * block = threads per block (32..1024, multiple of 32), unroll = independent
+ * loads in flight per thread (1, 2, 4 or 8).  0 keeps the current value. */
+SELL_API sell_status sell_set_launch(sell_handle h, int32_t block, int32_t unroll);
+
+/* Fill *info (host struct).  Errors: SELL_EINVAL. */
+SELL_API sell_status sell_info(sell_handle h, sell_info_t *info);
+
+/* Copy the format to host buffers (any may be NULL to skip it): val (stored
+ * elements of the storage type), col (stored), cs (nchunks + 1), cl
+ * (nchunks), rl (nchunks * C: length of every sorted row, 0 past nrows), perm
+ * (nrows; identity when sigma <= 1).  Synchronous.  Errors: SELL_EINVAL,
+ * SELL_ECUDA. */
+SELL_API sell_status sell_export(sell_handle h, void *val, int32_t *col, int64_t *cs, int32_t *cl,
+                        int32_t *rl, int32_t *perm);
+
+/* Release a handle and its device memory.  NULL is accepted (no-op). */
+SELL_API sell_status sell_free(sell_handle h);
+
+/* Static text for a status, and the calling thread's last error message. */
+SELL_API const char *sell_strerror(sell_status s);
+SELL_API const char *sell_last_error(void);
+
+/* ------------------------------------------------------------- batching */
+
+/* One product of a batch: Y = A X (or Y += A X) for k right-hand sides, with
+ * the layout rules of sell_spmmv (k = 1 and ldx = ldy = 1 is a plain SpMV).
+ * X and Y are device pointers. */
+typedef struct {
+    sell_handle A;
+    const void *X;
+    void *Y;
+    int64_t ldx, ldy;
+    int32_t k;
+    uint32_t flags;  /* SELL_SPMV_ACCUMULATE | SELL_SPMV_COMPENSATED */
+} sell_batch_item;
+
+typedef struct sell_batch *sell_batch_plan;
+
+/* Prepare a batch of n products for one persistent launch: a device table of
+ * work items (one per tile of 256 sorted rows of one product) that the
+ * persistent kernel's blocks claim with an atomic counter.  The products may
+ * use matrices of different sizes and storage types; a matrix with more than
+ * 8 right-hand sides is split into blocks of 8.  Each result is bit-identical
+ * to the same product run alone by sell_spmmv.  The plan owns its device
+ * table; the items' buffers are referenced, not copied.  Several products in
+ * one plan must not write overlapping Y.  Errors: SELL_EINVAL, SELL_ENOMEM,
+ * SELL_ECUDA. */
+SELL_API sell_status sell_batch_create(const sell_batch_item *items, int32_t n, void *stream,
+                              sell_batch_plan *out);
+
+/* Launch a plan on `stream` (capturable in a CUDA graph: one memset and one
+ * kernel).  grid = 0 picks one block per SM times the occupancy.
+ * Errors: SELL_EINVAL, SELL_ECUDA. */
+SELL_API sell_status sell_batch_run(sell_batch_plan plan, int32_t grid, void *stream);
+
+/* Release a plan (NULL accepted). */
+SELL_API sell_status sell_batch_free(sell_batch_plan plan);
+
+/* ------------------------------------------------------------ measuring */
+
+/* Read-only bandwidth kernel (the GPU analogue of Listing "reduction",
+ * Sec. 2.1): reads `bytes` of device memory at `buf` (16-byte aligned, size
+ * a multiple of 16) and writes one double per block to `sink` (device, at
+ * least `grid` doubles) so the reads cannot be elided.  grid = 0 picks
+ * 4 blocks per SM.  Used to measure the bandwidth b of the roofline model
+ * (Eq. "roof_general").  Errors: SELL_EINVAL, SELL_ECUDA. */
+SELL_API sell_status sell_bench_read(const void *buf, size_t bytes, double *sink, int32_t grid,
+                            void *stream);
+
+/* Binary64 fused multiply-add throughput kernel: every thread of
+ * grid x 256 threads runs `iters` x 64 dependent-chain FMAs on 8 independent
+ * chains; `sink` (device, grid*256 doubles) receives the results.  Used to
+ * measure the FP64 pipe's peak, a possible co-bound of the binary64 SpMV
+ * (one FMA per stored nonzero).  Errors: SELL_EINVAL, SELL_ECUDA. */
+SELL_API sell_status sell_bench_fma64(double *sink, int32_t grid, int32_t iters, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SELL_H */

@@ -1,0 +1,276 @@
+// sell_api.cu -- the extern "C" entry points declared in include/sell.h:
+// argument checks, error reporting, the allocator hook and handle lifetime.
+// The kernels live in sell_build.cu, sell_spmv.cu, sell_batch.cu and
+// sell_bench.cu.
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "sell_internal.cuh"
+
+namespace sell {
+
+namespace {
+thread_local std::string g_last_error;
+std::mutex g_alloc_mu;
+Allocator g_alloc;  // null callbacks = stream-ordered cudaMallocAsync
+}  // namespace
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+sell_status fail(sell_status s, const std::string &msg) {
+    g_last_error = msg;
+    return s;
+}
+
+sell_status cuda_fail(cudaError_t e, const char *what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    if (e == cudaErrorMemoryAllocation) return SELL_ENOMEM;
+    return SELL_ECUDA;
+}
+
+void *Allocator::get(size_t bytes, cudaStream_t s) const {
+    if (alloc) return alloc(bytes, ctx, s);
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+        (void)cudaGetLastError();  // clear the sticky-free allocation error
+        return nullptr;
+    }
+    return p;
+}
+
+void Allocator::put(void *p, cudaStream_t s) const {
+    if (!p) return;
+    if (release) release(p, ctx, s);
+    else (void)cudaFreeAsync(p, s);
+}
+
+Allocator current_allocator() {
+    std::lock_guard<std::mutex> g(g_alloc_mu);
+    return g_alloc;
+}
+
+sell_status DevBuf::alloc(const Allocator &a, size_t n, cudaStream_t s) {
+    reset();
+    al = a;
+    stream = s;
+    if (n == 0) return SELL_OK;
+    p = al.get(n, s);
+    if (!p) return fail(SELL_ENOMEM, "device allocation of " + std::to_string(n) + " bytes failed");
+    bytes = n;
+    return SELL_OK;
+}
+
+void DevBuf::reset() {
+    if (p) al.put(p, stream);
+    p = nullptr;
+    bytes = 0;
+}
+
+namespace {
+
+void free_matrix(sell_matrix *h) {
+    // every kernel that may still read the arrays must finish first
+    (void)cudaDeviceSynchronize();
+    void *ptrs[] = {h->val, h->col, h->cs, h->cl, h->srl, h->perm, h->xstage, h->ystage};
+    for (void *p : ptrs) h->al.put(p, nullptr);
+    (void)cudaDeviceSynchronize();
+    delete h;
+}
+
+sell_status ensure_stage(sell_matrix *h, void **buf, size_t *have, size_t need, cudaStream_t s) {
+    if (*have >= need) return SELL_OK;
+    if (*buf) {
+        SELL_CUDA_TRY(cudaStreamSynchronize(s));
+        h->al.put(*buf, s);
+        *buf = nullptr;
+        *have = 0;
+    }
+    *buf = h->al.get(need, s);
+    if (!*buf) return fail(SELL_ENOMEM, "host-io staging buffer allocation failed");
+    *have = need;
+    return SELL_OK;
+}
+
+}  // namespace
+}  // namespace sell
+
+using namespace sell;
+
+extern "C" {
+
+sell_status sell_set_allocator(sell_alloc_fn alloc, sell_free_fn release, void *ctx) {
+    if ((alloc == nullptr) != (release == nullptr))
+        return fail(SELL_EINVAL, "sell_set_allocator: give both callbacks or neither");
+    std::lock_guard<std::mutex> g(g_alloc_mu);
+    g_alloc.alloc = alloc;
+    g_alloc.release = release;
+    g_alloc.ctx = alloc ? ctx : nullptr;
+    return SELL_OK;
+}
+
+sell_status sell_build(const sell_csr *A, const sell_opts *opts, void *stream, sell_handle *out) {
+    if (!out) return fail(SELL_EINVAL, "sell_build: NULL output handle");
+    sell_matrix *h = new (std::nothrow) sell_matrix();
+    if (!h) return fail(SELL_ENOMEM, "sell_build: host allocation failed");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    h->device = dev;
+    sell_status st = build_format(A, opts, static_cast<cudaStream_t>(stream), h);
+    if (st != SELL_OK) {
+        std::string msg = g_last_error;
+        free_matrix(h);
+        g_last_error = msg;
+        return st;
+    }
+    *out = h;
+    return SELL_OK;
+}
+
+sell_status sell_spmmv(sell_handle h, const void *X, int64_t ldx, void *Y, int64_t ldy, int32_t k,
+                       uint32_t flags, void *stream) {
+    if (!h) return fail(SELL_EINVAL, "sell_spmmv: NULL handle");
+    if (k < 1 || ldx < k || ldy < k) return fail(SELL_EINVAL, "sell_spmmv: need k >= 1, ldx >= k, ldy >= k");
+    if (flags & ~(SELL_SPMV_ACCUMULATE | SELL_SPMV_COMPENSATED | SELL_SPMV_HOST_IO))
+        return fail(SELL_EINVAL, "sell_spmmv: unknown flags");
+    if ((flags & SELL_SPMV_COMPENSATED) && h->store_type == SELL_F64)
+        return fail(SELL_EUNSUPPORTED, "compensated accumulation needs F32/BF16 storage");
+    if (h->nrows == 0) return SELL_OK;
+    if (!Y || (!X && h->ncols > 0)) return fail(SELL_EINVAL, "sell_spmmv: NULL vector");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!(flags & SELL_SPMV_HOST_IO)) return launch_spmmv(h, X, ldx, Y, ldy, k, flags, s);
+
+    // host buffers: stage through device memory owned by the handle
+    const size_t xs = h->store_type == SELL_F64 ? 8 : 4;
+    const size_t xb = (size_t)h->ncols * ldx * xs, yb = (size_t)h->nrows * ldy * xs;
+    SELL_TRY(ensure_stage(h, &h->xstage, &h->xstage_bytes, xb > 0 ? xb : 16, s));
+    SELL_TRY(ensure_stage(h, &h->ystage, &h->ystage_bytes, yb, s));
+    if (xb) SELL_CUDA_TRY(cudaMemcpyAsync(h->xstage, X, xb, cudaMemcpyHostToDevice, s));
+    if (flags & SELL_SPMV_ACCUMULATE)
+        SELL_CUDA_TRY(cudaMemcpyAsync(h->ystage, Y, yb, cudaMemcpyHostToDevice, s));
+    SELL_TRY(launch_spmmv(h, h->xstage, ldx, h->ystage, ldy, k, flags & ~SELL_SPMV_HOST_IO, s));
+    SELL_CUDA_TRY(cudaMemcpyAsync(Y, h->ystage, yb, cudaMemcpyDeviceToHost, s));
+    return SELL_OK;
+}
+
+sell_status sell_spmv(sell_handle h, const void *x, void *y, uint32_t flags, void *stream) {
+    return sell_spmmv(h, x, 1, y, 1, 1, flags, stream);
+}
+
+sell_status sell_set_launch(sell_handle h, int32_t block, int32_t unroll) {
+    if (!h) return fail(SELL_EINVAL, "sell_set_launch: NULL handle");
+    if (block != 0 && (block < 32 || block > 1024 || block % 32 != 0))
+        return fail(SELL_EINVAL, "sell_set_launch: block must be a multiple of 32 in [32, 1024]");
+    if (unroll != 0 && unroll != 1 && unroll != 2 && unroll != 4 && unroll != 8)
+        return fail(SELL_EINVAL, "sell_set_launch: unroll must be 1, 2, 4 or 8");
+    if (block) h->block = block;
+    if (unroll) h->unroll = unroll;
+    return SELL_OK;
+}
+
+sell_status sell_info(sell_handle h, sell_info_t *info) {
+    if (!h || !info) return fail(SELL_EINVAL, "sell_info: NULL argument");
+    std::memset(info, 0, sizeof(*info));
+    info->nrows = h->nrows;
+    info->ncols = h->ncols;
+    info->nnz = h->nnz;
+    info->nchunks = h->nchunks;
+    info->stored = h->stored;
+    info->max_row_len = h->max_rl;
+    info->sigma = h->sigma;
+    info->C = h->C;
+    info->store_type = h->store_type;
+    info->flags = h->flags;
+    info->has_perm = h->perm != nullptr;
+    info->beta = h->beta;
+    info->zeta = h->zeta;
+    info->device_bytes = h->device_bytes;
+    return SELL_OK;
+}
+
+sell_status sell_export(sell_handle h, void *val, int32_t *col, int64_t *cs, int32_t *cl, int32_t *rl,
+                        int32_t *perm) {
+    if (!h) return fail(SELL_EINVAL, "sell_export: NULL handle");
+    SELL_CUDA_TRY(cudaDeviceSynchronize());
+    const size_t vs = value_size(h->store_type);
+    if (val && h->stored) SELL_CUDA_TRY(cudaMemcpy(val, h->val, h->stored * vs, cudaMemcpyDeviceToHost));
+    if (col && h->stored)
+        SELL_CUDA_TRY(cudaMemcpy(col, h->col, h->stored * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (cs) SELL_CUDA_TRY(cudaMemcpy(cs, h->cs, (h->nchunks + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    if (cl && h->nchunks)
+        SELL_CUDA_TRY(cudaMemcpy(cl, h->cl, h->nchunks * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (rl && h->nchunks)
+        SELL_CUDA_TRY(cudaMemcpy(rl, h->srl, h->nchunks * h->C * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (perm) {
+        if (h->perm) {
+            SELL_CUDA_TRY(cudaMemcpy(perm, h->perm, h->nrows * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        } else {
+            for (int64_t i = 0; i < h->nrows; ++i) perm[i] = (int32_t)i;
+        }
+    }
+    return SELL_OK;
+}
+
+sell_status sell_free(sell_handle h) {
+    if (h) free_matrix(h);
+    return SELL_OK;
+}
+
+const char *sell_strerror(sell_status s) {
+    switch (s) {
+        case SELL_OK: return "success";
+        case SELL_EINVAL: return "invalid argument";
+        case SELL_ENOMEM: return "out of memory";
+        case SELL_ECUDA: return "CUDA error";
+        case SELL_EBOUNDS: return "bounds check failed";
+        case SELL_ETIMEOUT: return "device wait timed out";
+        case SELL_EUNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char *sell_last_error(void) { return g_last_error.c_str(); }
+
+sell_status sell_batch_create(const sell_batch_item *items, int32_t n, void *stream, sell_batch_plan *out) {
+    if (!out || n < 0 || (n > 0 && !items)) return fail(SELL_EINVAL, "sell_batch_create: bad arguments");
+    sell_batch *b = new (std::nothrow) sell_batch();
+    if (!b) return fail(SELL_ENOMEM, "sell_batch_create: host allocation failed");
+    sell_status st = batch_create(items, n, static_cast<cudaStream_t>(stream), b);
+    if (st != SELL_OK) {
+        delete b;
+        return st;
+    }
+    *out = b;
+    return SELL_OK;
+}
+
+sell_status sell_batch_run(sell_batch_plan plan, int32_t grid, void *stream) {
+    if (!plan || grid < 0) return fail(SELL_EINVAL, "sell_batch_run: bad arguments");
+    return batch_run(plan, grid, static_cast<cudaStream_t>(stream));
+}
+
+sell_status sell_batch_free(sell_batch_plan plan) {
+    if (!plan) return SELL_OK;
+    (void)cudaDeviceSynchronize();
+    plan->al.put(plan->items, nullptr);
+    plan->al.put(plan->units, nullptr);
+    plan->al.put(plan->counter, nullptr);
+    (void)cudaDeviceSynchronize();
+    delete plan;
+    return SELL_OK;
+}
+
+sell_status sell_bench_read(const void *buf, size_t bytes, double *sink, int32_t grid, void *stream) {
+    return bench_read(buf, bytes, sink, grid, static_cast<cudaStream_t>(stream));
+}
+
+sell_status sell_bench_fma64(double *sink, int32_t grid, int32_t iters, void *stream) {
+    return bench_fma64(sink, grid, iters, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

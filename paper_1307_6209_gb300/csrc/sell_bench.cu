@@ -1,0 +1,84 @@
+// sell_bench.cu -- measuring kernels for the roofline model (Sec. 2.1, Sec. 4).
+//
+// k_read_bw is the GPU analogue of the read-only reduction benchmark of
+// Listing "reduction": every thread sums 16-byte vectors of a large buffer in
+// a grid-stride loop; one partial sum per block is written so that the loads
+// cannot be removed.  Its bandwidth is the b of Eq. "roof_general".
+//
+// k_fma64 measures the binary64 FMA issue rate, which bounds the binary64
+// SpMV as well (one FMA per stored nonzero).
+#include "sell_internal.cuh"
+
+namespace sell {
+namespace {
+
+__global__ void __launch_bounds__(512) k_read_bw(const double2 *__restrict__ a, int64_t n2,
+                                                 double *__restrict__ sink) {
+    __shared__ double red[16];
+    double s0 = 0.0, s1 = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < n2; i += 4 * stride) {
+        double2 v0 = __ldcs(a + i), v1 = __ldcs(a + i + stride);
+        double2 v2 = __ldcs(a + i + 2 * stride), v3 = __ldcs(a + i + 3 * stride);
+        s0 += (v0.x + v1.x) + (v2.x + v3.x);
+        s1 += (v0.y + v1.y) + (v2.y + v3.y);
+    }
+    for (; i < n2; i += stride) {
+        double2 v = __ldcs(a + i);
+        s0 += v.x;
+        s1 += v.y;
+    }
+    double s = s0 + s1;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        sink[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_fma64(double *__restrict__ sink, int iters) {
+    const double a = 1.0000001, b = 0.9999999;
+    double c[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) c[q] = threadIdx.x * 1e-3 + q;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int rep = 0; rep < 8; ++rep)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) c[q] = fma(c[q], a, b);
+    }
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t += c[q];
+    sink[blockIdx.x * (int64_t)blockDim.x + threadIdx.x] = t;
+}
+
+}  // namespace
+
+sell_status bench_read(const void *buf, size_t bytes, double *sink, int32_t grid, cudaStream_t s) {
+    if (!buf || !sink || bytes == 0 || (bytes % 16) != 0 || ((uintptr_t)buf % 16) != 0 || grid < 0)
+        return fail(SELL_EINVAL, "sell_bench_read: need a 16-byte aligned buffer, size % 16 == 0");
+    int g = grid;
+    if (g == 0) {
+        int dev = 0, sms = 0;
+        SELL_CUDA_TRY(cudaGetDevice(&dev));
+        SELL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        g = sms * 4;
+    }
+    k_read_bw<<<g, 512, 0, s>>>(static_cast<const double2 *>(buf), (int64_t)(bytes / 16), sink);
+    SELL_CUDA_TRY(cudaGetLastError());
+    return SELL_OK;
+}
+
+sell_status bench_fma64(double *sink, int32_t grid, int32_t iters, cudaStream_t s) {
+    if (!sink || grid < 1 || iters < 1) return fail(SELL_EINVAL, "sell_bench_fma64: bad arguments");
+    k_fma64<<<grid, 256, 0, s>>>(sink, iters);
+    SELL_CUDA_TRY(cudaGetLastError());
+    return SELL_OK;
+}
+
+}  // namespace sell

@@ -1,0 +1,108 @@
+"""Failure handling through the C ABI, made on the host: malformed CRS input,
+bad options, and an allocator that fails on demand (no GPU fault involved)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1307_6209_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _status(fn, *a, **k):
+    from paper_1307_6209_gb300 import sell
+    try:
+        fn(*a, **k)
+    except sell.SellError as e:
+        return e.status
+    return sell.SELL_OK
+
+
+def test_malformed_csr_is_einval():
+    import torch
+    from paper_1307_6209_gb300 import sell
+
+    A = synth.lognormal(500, seed=1, cap=50)
+    bad = []
+    B = synth.CSR(A.nrows, A.ncols, A.rpt.copy(), A.col.copy(), A.val)
+    B.rpt[0] = 1
+    bad.append(B)
+    B = synth.CSR(A.nrows, A.ncols, A.rpt.copy(), A.col.copy(), A.val)
+    B.rpt[10], B.rpt[11] = B.rpt[11], B.rpt[10]  # decreasing somewhere
+    bad.append(B)
+    B = synth.CSR(A.nrows, A.ncols, A.rpt.copy(), A.col.copy(), A.val)
+    B.col[7] = A.ncols  # out of range
+    bad.append(B)
+    B = synth.CSR(A.nrows, A.ncols, A.rpt.copy(), A.col.copy(), A.val)
+    B.col[3] = -1
+    bad.append(B)
+    for B in bad:
+        assert _status(sell.sell_build, B, C=32, sigma=64) == sell.SELL_EINVAL
+        Bd = synth.CSR(B.nrows, B.ncols, torch.from_numpy(B.rpt).cuda(), torch.from_numpy(B.col).cuda(),
+                       torch.from_numpy(B.val).cuda())
+        assert _status(sell.sell_build, Bd, C=32, sigma=64) == sell.SELL_EINVAL
+    assert "malformed" in sell.sell_last_error() or "rpt" in sell.sell_last_error()
+
+
+def test_bad_options_are_einval():
+    from paper_1307_6209_gb300 import sell
+
+    A = synth.random_csr(40, 30, density=0.2, seed=0)
+    assert _status(sell.sell_build, A, C=0) == sell.SELL_EINVAL
+    assert _status(sell.sell_build, A, C=32, sigma=0) == sell.SELL_EINVAL
+    assert _status(sell.sell_build, A, C=32, store_type=9) == sell.SELL_EINVAL
+    assert _status(sell.sell_build, A, C=32, flags=sell.SELL_BUILD_PERMUTE_COLS) == sell.SELL_EINVAL
+    assert _status(sell.sell_build, A, C=32, flags=0x80) == sell.SELL_EINVAL
+    h = sell.sell_build(synth.laplace2d(8), C=32)
+    assert _status(sell.sell_set_launch, h, 48, 0) == sell.SELL_EINVAL
+    assert _status(sell.sell_set_launch, h, 0, 3) == sell.SELL_EINVAL
+    lib = sell.load()
+    assert lib.sell_spmmv(h.handle, None, 1, None, 1, 0, 0, None) == sell.SELL_EINVAL
+    assert lib.sell_spmv(None, None, None, 0, None) == sell.SELL_EINVAL
+    assert lib.sell_free(None) == sell.SELL_OK
+
+
+def test_failing_allocator_reports_enomem_without_leak():
+    """An allocator that fails at the n-th request: sell_build must return
+    SELL_ENOMEM and give back every buffer it obtained."""
+    import torch
+    from paper_1307_6209_gb300 import sell
+
+    lib = sell.load()
+    A = synth.lognormal(20000, seed=2, cap=500)
+    live = set()
+    state = {"n": 0, "fail_at": -1}
+
+    def _alloc(nbytes, ctx, stream):
+        state["n"] += 1
+        if state["n"] == state["fail_at"]:
+            return None
+        p = torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), stream or 0)
+        live.add(p)
+        return p
+
+    def _free(ptr, ctx, stream):
+        if ptr:
+            live.discard(ptr)
+            torch.cuda.caching_allocator_delete(ptr)
+
+    a, f = sell.ALLOC_FN(_alloc), sell.FREE_FN(_free)
+    assert lib.sell_set_allocator(a, f, None) == sell.SELL_OK
+    try:
+        # count the requests of a successful build (radix path: many buffers)
+        state["fail_at"] = -1
+        state["n"] = 0
+        h = sell.sell_build(A, C=32, sigma=8192)
+        total = state["n"]
+        h.free()
+        torch.cuda.synchronize()
+        assert not live and total >= 8
+        for k in range(1, total + 1):
+            state["n"] = 0
+            state["fail_at"] = k
+            assert _status(sell.sell_build, A, C=32, sigma=8192) == sell.SELL_ENOMEM
+            torch.cuda.synchronize()
+            assert not live, f"leak after failing request {k}"
+    finally:
+        assert lib.sell_set_allocator(sell.ALLOC_FN(), sell.FREE_FN(), None) == sell.SELL_OK

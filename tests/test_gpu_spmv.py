@@ -1,0 +1,128 @@
+"""GPU SpMV / SpMMV parity against the CPU oracle (binary64 storage).
+
+y must agree with Listing "crs" (binary64, CRS order, no FMA) within the
+row-wise bound of tests/gpu_util.tol_f64; results of the CUDA path must be
+bitwise identical across (C, sigma), launch shapes and right-hand-side
+blocking, because every row is one FMA chain in CRS order.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1307_6209_gb300 import synth
+from tests.gpu_util import oracle_reference, parity_matrices, tol_f64
+
+pytestmark = pytest.mark.gpu
+
+
+def _spmv(h, x, y0=None, flags=0):
+    import torch
+    from paper_1307_6209_gb300 import sell
+
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    if y0 is None:
+        yd = torch.full((h.info.nrows,), float("nan"), dtype=torch.float64, device="cuda")
+    else:
+        yd = torch.from_numpy(np.ascontiguousarray(y0)).cuda()
+    sell.sell_spmv(h, xd, yd, flags=flags)
+    torch.cuda.synchronize()
+    return yd.cpu().numpy()
+
+
+@pytest.mark.parametrize("name,A", parity_matrices(), ids=lambda v: v if isinstance(v, str) else "")
+def test_spmv_matches_oracle_and_is_invariant(name, A):
+    from paper_1307_6209_gb300 import sell
+
+    x = synth.vector(A.ncols, seed=0)
+    ref, scale, rl = oracle_reference(A, x)
+    first = None
+    for C, sigma in [(32, 1), (1, 1), (2, 7), (32, 256), (64, 4096), (128, 10 ** 9), (3, 5000)]:
+        h = sell.sell_build(A, C=C, sigma=sigma)
+        for block, unroll in [(256, 4), (128, 1), (512, 8), (1024, 2)]:
+            sell.sell_set_launch(h, block, unroll)
+            y = _spmv(h, x)
+            assert np.all(np.abs(y - ref) <= tol_f64(rl, scale)), (C, sigma, block, unroll)
+            if first is None:
+                first = y
+            assert y.tobytes() == first.tobytes(), "result depends on (C, sigma) or launch shape"
+        h.free()
+
+
+def test_spmv_accumulate():
+    from paper_1307_6209_gb300 import sell
+
+    A = synth.lognormal(3000, seed=3, cap=200)
+    x = synth.vector(A.ncols, seed=1)
+    y0 = synth.vector(A.nrows, seed=2)
+    ref = oracle.csr_spmv(A, x, y0=y0, accumulate=True)
+    scale = oracle.csr_absdot(A, x) + np.abs(y0)
+    for sigma in (1, 512):
+        h = sell.sell_build(A, C=32, sigma=sigma)
+        y = _spmv(h, x, y0=y0, flags=sell.SELL_SPMV_ACCUMULATE)
+        assert np.all(np.abs(y - ref) <= tol_f64(A.row_lengths() + 1, scale))
+
+
+def test_spmv_permuted_space():
+    """With the symmetric permutation the handle maps x' = Px to y' = Py."""
+    from paper_1307_6209_gb300 import sell
+
+    A = synth.lognormal(4001, seed=4, cap=150)
+    x = synth.vector(A.ncols, seed=3)
+    ref, scale, rl = oracle_reference(A, x)
+    h = sell.sell_build(A, C=32, sigma=1024, flags=sell.SELL_BUILD_PERMUTE_COLS)
+    perm = sell.sell_export(h)["perm"]
+    yp = _spmv(h, x[perm])
+    assert np.all(np.abs(yp - ref[perm]) <= tol_f64(rl[perm], scale[perm]))
+
+
+def test_spmv_host_io():
+    """HOST_IO: numpy in, numpy out; the library stages the copies."""
+    from paper_1307_6209_gb300 import sell
+    import torch
+
+    A = synth.lognormal(5000, seed=5, cap=100)
+    x = synth.vector(A.ncols, seed=4)
+    ref, scale, rl = oracle_reference(A, x)
+    h = sell.sell_build(A, C=32, sigma=256)
+    y = np.full(A.nrows, np.nan)
+    for _ in range(2):
+        sell.sell_spmv(h, x, y, flags=sell.SELL_SPMV_HOST_IO)
+        torch.cuda.synchronize()
+        assert np.all(np.abs(y - ref) <= tol_f64(rl, scale))
+    assert y.tobytes() == _spmv(h, x).tobytes()
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 8, 11, 16])
+def test_spmmv_columns_bitwise_equal_spmv(k):
+    import torch
+    from paper_1307_6209_gb300 import sell
+
+    A = synth.lognormal(3001, seed=6, cap=120)
+    X = synth.block(A.ncols, k, seed=5)
+    h = sell.sell_build(A, C=32, sigma=128)
+    for ld_pad in (0, 3):
+        Xd = torch.zeros((A.ncols, k + ld_pad), dtype=torch.float64, device="cuda")
+        Xd[:, :k] = torch.from_numpy(X).cuda()
+        Yd = torch.full((A.nrows, k + ld_pad), float("nan"), dtype=torch.float64, device="cuda")
+        sell.sell_spmmv(h, Xd[:, :k], Yd[:, :k])
+        torch.cuda.synchronize()
+        Y = Yd[:, :k].cpu().numpy()
+        Yref = oracle.csr_spmmv(A, X)
+        for c in range(k):
+            yc = _spmv(h, X[:, c])
+            assert Y[:, c].tobytes() == yc.tobytes(), f"column {c} differs from SpMV"
+            scale = oracle.csr_absdot(A, X[:, c])
+            assert np.all(np.abs(Y[:, c] - Yref[:, c]) <= tol_f64(A.row_lengths(), scale))
+        if ld_pad:
+            assert torch.isnan(Yd[:, k:]).all(), "wrote outside the k columns"
+
+
+def test_spmv_empty_matrix_is_noop():
+    import torch
+    from paper_1307_6209_gb300 import sell
+
+    A = synth.CSR(0, 0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    h = sell.sell_build(A, C=32, sigma=1)
+    sell.sell_spmv(h, torch.empty(0, dtype=torch.float64, device="cuda"),
+                   torch.empty(0, dtype=torch.float64, device="cuda"))
+    assert h.info.stored == 0 and h.info.nchunks == 0
