@@ -171,7 +171,7 @@ SELL_API sell_status sell_spmmv(sell_handle h, const void *X, int64_t ldx, void 
                        int32_t k, uint32_t flags, void *stream);
 
 /* Launch tuning of a handle's SpMV/SpMMV kernels (autotuner knob):
- * block = threads per block (32..1024, multiple of 32), unroll = independent
+ * block = threads per block (32..512, multiple of 32), unroll = independent
  * loads in flight per thread (1, 2, 4 or 8).  0 keeps the current value. */
 SELL_API sell_status sell_set_launch(sell_handle h, int32_t block, int32_t unroll);
 

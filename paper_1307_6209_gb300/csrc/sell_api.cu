@@ -73,7 +73,7 @@ namespace {
 void free_matrix(sell_matrix *h) {
     // every kernel that may still read the arrays must finish first
     (void)cudaDeviceSynchronize();
-    void *ptrs[] = {h->val, h->col, h->cs, h->cl, h->srl, h->perm, h->xstage, h->ystage};
+    void *ptrs[] = {h->val, h->col, h->cs, h->cl, h->srl, h->perm, h->lchunk, h->xstage, h->ystage};
     for (void *p : ptrs) h->al.put(p, nullptr);
     (void)cudaDeviceSynchronize();
     delete h;
@@ -164,8 +164,8 @@ sell_status sell_spmv(sell_handle h, const void *x, void *y, uint32_t flags, voi
 
 sell_status sell_set_launch(sell_handle h, int32_t block, int32_t unroll) {
     if (!h) return fail(SELL_EINVAL, "sell_set_launch: NULL handle");
-    if (block != 0 && (block < 32 || block > 1024 || block % 32 != 0))
-        return fail(SELL_EINVAL, "sell_set_launch: block must be a multiple of 32 in [32, 1024]");
+    if (block != 0 && (block < 32 || block > 512 || block % 32 != 0))
+        return fail(SELL_EINVAL, "sell_set_launch: block must be a multiple of 32 in [32, 512]");
     if (unroll != 0 && unroll != 1 && unroll != 2 && unroll != 4 && unroll != 8)
         return fail(SELL_EINVAL, "sell_set_launch: unroll must be 1, 2, 4 or 8");
     if (block) h->block = block;

@@ -13,7 +13,7 @@
 #include <algorithm>
 #include <vector>
 
-#include "sell_internal.cuh"
+#include "sell_rowdot.cuh"
 
 namespace sell {
 namespace {
@@ -25,6 +25,7 @@ struct Prod {
     const int32_t *col;
     const int64_t *cs;
     const int32_t *srl;
+    const int32_t *cl;
     const int32_t *perm;
     const void *X;
     void *Y;
@@ -32,96 +33,39 @@ struct Prod {
     int32_t C, kb, type, acc, comp, vec;
 };
 
+// kind 0: a tile of kTileRows sorted rows starting at idx (its short rows);
+// kind 1: the long rows of chunk idx (one block, many threads per row).
 struct Unit {
     int32_t prod;
-    int32_t row0;
+    int32_t kind;
+    int64_t idx;
 };
 
-__device__ __forceinline__ double widen_b(double v) { return v; }
-__device__ __forceinline__ float widen_b(float v) { return v; }
-__device__ __forceinline__ float widen_b(__nv_bfloat16 v) { return __bfloat162float(v); }
-
-struct PlainD {
-    double s;
-    __device__ __forceinline__ void init(double y) { s = y; }
-    __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
-    __device__ __forceinline__ double result() const { return s; }
-};
-struct PlainF {
-    float s;
-    __device__ __forceinline__ void init(float y) { s = y; }
-    __device__ __forceinline__ void add(float a, float b) { s = fmaf(a, b, s); }
-    __device__ __forceinline__ float result() const { return s; }
-};
-struct Dot2F {
-    float p, s;
-    __device__ __forceinline__ void init(float y) { p = y; s = 0.0f; }
-    __device__ __forceinline__ void add(float a, float b) {
-        float h = __fmul_rn(a, b);
-        float r = __fmaf_rn(a, b, -h);
-        float t = __fadd_rn(p, h);
-        float z = __fsub_rn(t, p);
-        float q = __fadd_rn(__fsub_rn(p, __fsub_rn(t, z)), __fsub_rn(h, z));
-        p = t;
-        s = __fadd_rn(s, __fadd_rn(q, r));
-    }
-    __device__ __forceinline__ float result() const { return __fadd_rn(p, s); }
-};
-
-template <class VT, class XT, int K, class Acc>
-__device__ __forceinline__ void row_product(const Prod &P, int64_t r, uint64_t pol) {
-    const int64_t c = r / P.C;
-    const int l = (int)(r - c * P.C);
-    const int len = P.srl[r];
-    const int64_t out = P.perm ? (int64_t)P.perm[r] : r;
-    const VT *vp = static_cast<const VT *>(P.val) + P.cs[c] + l;
-    const int32_t *cp = P.col + P.cs[c] + l;
+template <class VT, int K, class Acc>
+__device__ __noinline__ void do_unit(const Prod &P, const Unit &u, uint64_t pol, void *smem) {
+    using XT = typename XType<VT>::T;
+    constexpr int U = K >= 8 ? 2 : (K >= 4 ? 4 : 8);
+    const VT *val = static_cast<const VT *>(P.val);
     const XT *X = static_cast<const XT *>(P.X);
     XT *Y = static_cast<XT *>(P.Y);
-    Acc acc[K];
-#pragma unroll
-    for (int q = 0; q < K; ++q) acc[q].init(P.acc ? Y[out * P.ldy + q] : XT(0));
-    constexpr int U = K >= 4 ? 2 : 4;
-    int j = 0;
-    for (; j + U <= len; j += U) {
-        VT v[U];
-        int32_t ci[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            v[u] = ld_stream(vp + (int64_t)u * P.C, pol);
-            ci[u] = ld_stream(cp + (int64_t)u * P.C, pol);
-        }
-        XT xv[U][K];
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-#pragma unroll
-            for (int q = 0; q < K; ++q) xv[u][q] = __ldg(X + (int64_t)ci[u] * P.ldx + q);
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-#pragma unroll
-            for (int q = 0; q < K; ++q) acc[q].add(widen_b(v[u]), xv[u][q]);
-        vp += (int64_t)U * P.C;
-        cp += (int64_t)U * P.C;
+    if (u.kind == 1) {
+        long_chunk<VT, XT, K, U, Acc>(val, P.col, P.cs, P.srl, P.cl, P.perm, X, P.ldx, Y, P.ldy, P.N, P.C,
+                                      u.idx, P.acc, P.vec != 0, pol, static_cast<Acc *>(smem));
+    } else {
+        const int64_t r = u.idx + threadIdx.x;
+        if (r < P.N)
+            short_row<VT, XT, K, U, Acc>(val, P.col, P.cs, P.srl, P.perm, X, P.ldx, Y, P.ldy, P.C, r, P.acc,
+                                         P.vec != 0, pol);
     }
-    for (; j < len; ++j) {
-        VT v = ld_stream(vp, pol);
-        int32_t ci = ld_stream(cp, pol);
-#pragma unroll
-        for (int q = 0; q < K; ++q) acc[q].add(widen_b(v), __ldg(X + (int64_t)ci * P.ldx + q));
-        vp += P.C;
-        cp += P.C;
-    }
-#pragma unroll
-    for (int q = 0; q < K; ++q) Y[out * P.ldy + q] = acc[q].result();
 }
 
-template <class VT, class XT, class Acc>
-__device__ __forceinline__ void row_dispatch_k(const Prod &P, int64_t r, uint64_t pol) {
+template <class VT, class Acc>
+__device__ __forceinline__ void dispatch_k(const Prod &P, const Unit &u, uint64_t pol, void *smem) {
     switch (P.kb) {
-        case 1: row_product<VT, XT, 1, Acc>(P, r, pol); break;
-        case 2: row_product<VT, XT, 2, Acc>(P, r, pol); break;
-        case 4: row_product<VT, XT, 4, Acc>(P, r, pol); break;
-        default: row_product<VT, XT, 8, Acc>(P, r, pol); break;
+        case 1: do_unit<VT, 1, Acc>(P, u, pol, smem); break;
+        case 2: do_unit<VT, 2, Acc>(P, u, pol, smem); break;
+        case 4: do_unit<VT, 4, Acc>(P, u, pol, smem); break;
+        default: do_unit<VT, 8, Acc>(P, u, pol, smem); break;
     }
 }
 
@@ -129,6 +73,7 @@ __global__ void __launch_bounds__(kTileRows)
 k_batch(const Prod *__restrict__ prods, const Unit *__restrict__ units, int64_t nwork,
         unsigned int *counter) {
     __shared__ int64_t s_unit;
+    __shared__ __align__(16) unsigned char part[kTileRows * 8 * 8];  // block x K(8) x 8-byte Acc
     const uint64_t pol = l2_evict_first_policy();
     for (;;) {
         if (threadIdx.x == 0) s_unit = (int64_t)atomicAdd(counter, 1u);
@@ -138,18 +83,16 @@ k_batch(const Prod *__restrict__ prods, const Unit *__restrict__ units, int64_t 
         if (w >= nwork) break;
         const Unit u = units[w];
         const Prod P = prods[u.prod];
-        const int64_t r = (int64_t)u.row0 + threadIdx.x;
-        if (r < P.N) {
-            if (P.type == SELL_F64) {
-                row_dispatch_k<double, double, PlainD>(P, r, pol);
-            } else if (P.type == SELL_F32) {
-                if (P.comp) row_dispatch_k<float, float, Dot2F>(P, r, pol);
-                else row_dispatch_k<float, float, PlainF>(P, r, pol);
-            } else {
-                if (P.comp) row_dispatch_k<__nv_bfloat16, float, Dot2F>(P, r, pol);
-                else row_dispatch_k<__nv_bfloat16, float, PlainF>(P, r, pol);
-            }
+        if (P.type == SELL_F64) {
+            dispatch_k<double, Plain<double>>(P, u, pol, part);
+        } else if (P.type == SELL_F32) {
+            if (P.comp) dispatch_k<float, Dot2>(P, u, pol, part);
+            else dispatch_k<float, Plain<float>>(P, u, pol, part);
+        } else {
+            if (P.comp) dispatch_k<__nv_bfloat16, Dot2>(P, u, pol, part);
+            else dispatch_k<__nv_bfloat16, Plain<float>>(P, u, pol, part);
         }
+        __syncthreads();
     }
 }
 
@@ -157,6 +100,7 @@ k_batch(const Prod *__restrict__ prods, const Unit *__restrict__ units, int64_t 
 
 sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s, sell_batch *b) {
     std::vector<Prod> prods;
+    std::vector<const sell_matrix *> owner;
     std::vector<std::pair<int64_t, int32_t>> order;  // (stored elements, product) for ordering
     for (int32_t i = 0; i < n; ++i) {
         const sell_batch_item &it = items[i];
@@ -178,6 +122,7 @@ sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s
             P.col = h->col;
             P.cs = h->cs;
             P.srl = h->srl;
+            P.cl = h->cl;
             P.perm = (h->flags & SELL_BUILD_PERMUTE_COLS) ? nullptr : h->perm;
             P.X = static_cast<const char *>(it.X) + done * xs;
             P.Y = static_cast<char *>(it.Y) + done * xs;
@@ -189,10 +134,11 @@ sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s
             P.type = h->store_type;
             P.acc = (it.flags & SELL_SPMV_ACCUMULATE) ? 1 : 0;
             P.comp = (it.flags & SELL_SPMV_COMPENSATED) ? 1 : 0;
-            P.vec = 0;
+            P.vec = (((uintptr_t)P.X % 16) == 0 && ((it.ldx * xs) % 16) == 0) ? 1 : 0;
             if (h->nrows > 0) {
                 order.push_back({h->stored * kb, (int32_t)prods.size()});
                 prods.push_back(P);
+                owner.push_back(h);
             }
             done += kb;
         }
@@ -202,10 +148,18 @@ sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s
                      [](const std::pair<int64_t, int32_t> &a, const std::pair<int64_t, int32_t> &b) {
                          return a.first > b.first;
                      });
+    // long-row chunks first (they have the longest critical path), then row tiles
     std::vector<Unit> units;
     for (auto &o : order) {
+        const sell_matrix *h = owner[o.second];
+        if (h->nlong == 0) continue;
+        std::vector<int32_t> lc((size_t)h->nlong);
+        SELL_CUDA_TRY(cudaMemcpy(lc.data(), h->lchunk, h->nlong * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        for (int32_t c : lc) units.push_back({o.second, 1, (int64_t)c});
+    }
+    for (auto &o : order) {
         const Prod &P = prods[o.second];
-        for (int64_t r0 = 0; r0 < P.N; r0 += kTileRows) units.push_back({o.second, (int32_t)r0});
+        for (int64_t r0 = 0; r0 < P.N; r0 += kTileRows) units.push_back({o.second, 0, r0});
     }
     b->al = current_allocator();
     b->nprod = (int32_t)prods.size();

@@ -12,31 +12,34 @@
 namespace sell {
 namespace {
 
-__global__ void __launch_bounds__(512) k_read_bw(const double2 *__restrict__ a, int64_t n2,
+// The loaded words are combined with integer adds: on GB300 the binary64 pipe
+// is too slow to keep up with HBM, so a floating-point sum would measure the
+// FP64 adder instead of the memory.
+__global__ void __launch_bounds__(512) k_read_bw(const uint4 *__restrict__ a, int64_t n16,
                                                  double *__restrict__ sink) {
-    __shared__ double red[16];
-    double s0 = 0.0, s1 = 0.0;
+    __shared__ unsigned int red[16];
+    unsigned int s0 = 0, s1 = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    for (; i + 3 * stride < n2; i += 4 * stride) {
-        double2 v0 = __ldcs(a + i), v1 = __ldcs(a + i + stride);
-        double2 v2 = __ldcs(a + i + 2 * stride), v3 = __ldcs(a + i + 3 * stride);
-        s0 += (v0.x + v1.x) + (v2.x + v3.x);
-        s1 += (v0.y + v1.y) + (v2.y + v3.y);
+    for (; i + 3 * stride < n16; i += 4 * stride) {
+        uint4 v0 = __ldcs(a + i), v1 = __ldcs(a + i + stride);
+        uint4 v2 = __ldcs(a + i + 2 * stride), v3 = __ldcs(a + i + 3 * stride);
+        s0 += (v0.x + v0.y) + (v1.x + v1.y) + (v2.x + v2.y) + (v3.x + v3.y);
+        s1 += (v0.z + v0.w) + (v1.z + v1.w) + (v2.z + v2.w) + (v3.z + v3.w);
     }
-    for (; i < n2; i += stride) {
-        double2 v = __ldcs(a + i);
-        s0 += v.x;
-        s1 += v.y;
+    for (; i < n16; i += stride) {
+        uint4 v = __ldcs(a + i);
+        s0 += v.x + v.y;
+        s1 += v.z + v.w;
     }
-    double s = s0 + s1;
+    unsigned int s = s0 + s1;
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t = 0.0;
+        unsigned int t = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        sink[blockIdx.x] = t;
+        sink[blockIdx.x] = (double)t;
     }
 }
 
@@ -69,7 +72,7 @@ sell_status bench_read(const void *buf, size_t bytes, double *sink, int32_t grid
         SELL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         g = sms * 4;
     }
-    k_read_bw<<<g, 512, 0, s>>>(static_cast<const double2 *>(buf), (int64_t)(bytes / 16), sink);
+    k_read_bw<<<g, 512, 0, s>>>(static_cast<const uint4 *>(buf), (int64_t)(bytes / 16), sink);
     SELL_CUDA_TRY(cudaGetLastError());
     return SELL_OK;
 }

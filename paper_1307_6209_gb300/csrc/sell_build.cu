@@ -319,6 +319,20 @@ __global__ void k_chunk_len(const int32_t *__restrict__ rl, const int32_t *__res
     }
 }
 
+// ---------------------------------------------------------- long-row chunks
+__global__ void k_long_flags(const int32_t *__restrict__ cl, int64_t Nc, int32_t *__restrict__ flag) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < Nc; c += stride)
+        flag[c] = cl[c] > kSeg ? 1 : 0;
+}
+
+__global__ void k_long_compact(const int32_t *__restrict__ cl, const int64_t *__restrict__ pos, int64_t Nc,
+                               int32_t *__restrict__ lchunk) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < Nc; c += stride)
+        if (cl[c] > kSeg) lchunk[pos[c]] = (int32_t)c;
+}
+
 // ------------------------------------------------------------------ scatter
 template <class TI, class TO> __device__ __forceinline__ TO cvt(TI v);
 template <> __device__ __forceinline__ double cvt<double, double>(double v) { return v; }
@@ -559,13 +573,31 @@ sell_status build_format(const sell_csr *A, const sell_opts *o, cudaStream_t s, 
                                       permute_cols ? inv.as<int32_t>() : nullptr);
         SELL_CUDA_TRY(cudaGetLastError());
     }
-    // 5. chunk offsets
+    // 5. chunk offsets, and the chunks that hold rows longer than kSeg
     SELL_TRY(cs.alloc(al, (Nc + 1) * sizeof(int64_t), s));
     SELL_TRY(scan_exclusive<int32_t>(cl.as<int32_t>(), C, Nc, cs.as<int64_t>(), al, s));
-    int64_t stored = 0;
+    DevBuf lflag, lpos;
+    if (Nc > 0) {
+        SELL_TRY(lflag.alloc(al, Nc * sizeof(int32_t), s));
+        SELL_TRY(lpos.alloc(al, (Nc + 1) * sizeof(int64_t), s));
+        k_long_flags<<<grid_for(Nc, 256), 256, 0, s>>>(cl.as<int32_t>(), Nc, lflag.as<int32_t>());
+        SELL_CUDA_TRY(cudaGetLastError());
+        SELL_TRY(scan_exclusive<int32_t>(lflag.as<int32_t>(), 1, Nc, lpos.as<int64_t>(), al, s));
+    }
+    int64_t stored = 0, nlong = 0;
     SELL_CUDA_TRY(cudaMemcpyAsync(&stored, cs.as<int64_t>() + Nc, sizeof(int64_t),
                                   cudaMemcpyDeviceToHost, s));
+    if (Nc > 0)
+        SELL_CUDA_TRY(cudaMemcpyAsync(&nlong, lpos.as<int64_t>() + Nc, sizeof(int64_t),
+                                      cudaMemcpyDeviceToHost, s));
     SELL_CUDA_TRY(cudaStreamSynchronize(s));
+    DevBuf lchunk;
+    if (nlong > 0) {
+        SELL_TRY(lchunk.alloc(al, nlong * sizeof(int32_t), s));
+        k_long_compact<<<grid_for(Nc, 256), 256, 0, s>>>(cl.as<int32_t>(), lpos.as<int64_t>(), Nc,
+                                                         lchunk.as<int32_t>());
+        SELL_CUDA_TRY(cudaGetLastError());
+    }
 
     // 6. values and columns
     DevBuf val, col;
@@ -606,7 +638,9 @@ sell_status build_format(const sell_csr *A, const sell_opts *o, cudaStream_t s, 
         h->zeta = 0.0;
     }
     h->al = al;
-    h->device_bytes = val.bytes + col.bytes + cs.bytes + cl.bytes + srl.bytes + perm.bytes;
+    h->nlong = nlong;
+    h->device_bytes = val.bytes + col.bytes + cs.bytes + cl.bytes + srl.bytes + perm.bytes + lchunk.bytes;
+    h->lchunk = (int32_t *)lchunk.release_ownership();
     h->val = val.release_ownership();
     h->col = (int32_t *)col.release_ownership();
     h->cs = (int64_t *)cs.release_ownership();

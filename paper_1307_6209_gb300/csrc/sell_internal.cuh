@@ -54,6 +54,11 @@ struct DevBuf {
     template <class T> T *as() const { return static_cast<T *>(p); }
 };
 
+// Entries per segment of a long row.  Part of the numerics: a row longer than
+// kSeg is summed segment by segment (sell_rowdot.cuh), so changing it changes
+// the rounding of long rows.
+constexpr int kSeg = 64;
+
 inline size_t value_size(int t) { return t == SELL_F64 ? 8 : (t == SELL_F32 ? 4 : 2); }
 
 }  // namespace sell
@@ -74,6 +79,8 @@ struct sell_matrix {
     int32_t *cl = nullptr;     // nchunks
     int32_t *srl = nullptr;    // nchunks * C, length of each sorted row
     int32_t *perm = nullptr;   // nrows, sorted -> original (null: identity)
+    int32_t *lchunk = nullptr; // nlong chunks holding rows longer than kSeg
+    int64_t nlong = 0;
     // host-io staging (lazily allocated)
     void *xstage = nullptr, *ystage = nullptr;
     size_t xstage_bytes = 0, ystage_bytes = 0;

@@ -1,0 +1,79 @@
+"""The binary64 kernels' documented arithmetic, checked bit for bit.
+
+A row of length L <= 64 is one FMA chain in CRS order from y0 (0, or the old
+y when accumulating); a longer row is cut into segments of 64 entries, each an
+FMA chain (segment 0 from y0, the others from 0), and the segment results are
+added in order.  Here every FMA and every addition is emulated exactly with
+rational arithmetic and one correct rounding to binary64 (float(Fraction) is
+correctly rounded), so the GPU result must match to the last bit."""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_1307_6209_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+SEG = 64
+
+
+def _rnd(q: Fraction) -> float:
+    return float(q)
+
+
+def _chain(vals, xs, y0):
+    s = float(y0)
+    for a, b in zip(vals, xs):
+        s = _rnd(Fraction(a) * Fraction(b) + Fraction(s))
+    return s
+
+
+def _row_result(vals, xs, y0):
+    L = len(vals)
+    if L <= SEG:
+        return _chain(vals, xs, y0)
+    parts = [_chain(vals[s:s + SEG], xs[s:s + SEG], y0 if s == 0 else 0.0) for s in range(0, L, SEG)]
+    t = parts[0]
+    for p in parts[1:]:
+        t = _rnd(Fraction(t) + Fraction(p))
+    return t
+
+
+def _matrix():
+    lens = [0, 1, 5, 63, 64, 65, 100, 127, 128, 129, 192, 200, 257, 640, 1000, 3]
+    rng = np.random.default_rng(42)
+    n = 2048
+    rows = []
+    for i in range(300):
+        L = lens[i % len(lens)] if i < 64 else int(rng.integers(0, 40))
+        rows.append(np.sort(rng.choice(n, size=L, replace=False)))
+    rl = np.array([len(r) for r in rows])
+    col = np.concatenate(rows).astype(np.int32)
+    val = rng.standard_normal(col.shape[0])
+    rpt = np.zeros(len(rows) + 1, np.int64)
+    np.cumsum(rl, out=rpt[1:])
+    return synth.CSR(len(rows), n, rpt, col, val)
+
+
+@pytest.mark.parametrize("accumulate", [False, True])
+def test_f64_rows_match_documented_arithmetic(accumulate):
+    import torch
+    from paper_1307_6209_gb300 import sell
+
+    A = _matrix()
+    x = synth.vector(A.ncols, seed=9)
+    y0 = synth.vector(A.nrows, seed=10)
+    expect = np.array([
+        _row_result(A.val[A.rpt[i]:A.rpt[i + 1]], x[A.col[A.rpt[i]:A.rpt[i + 1]]], y0[i] if accumulate else 0.0)
+        for i in range(A.nrows)])
+    flags = sell.SELL_SPMV_ACCUMULATE if accumulate else 0
+    for C, sigma, block in [(32, 1, 256), (32, 10 ** 9, 512), (64, 128, 64), (1, 1, 32), (128, 4, 128)]:
+        h = sell.sell_build(A, C=C, sigma=sigma)
+        sell.sell_set_launch(h, block, 4)
+        xd = torch.from_numpy(x).cuda()
+        yd = torch.from_numpy(y0.copy()).cuda()
+        sell.sell_spmv(h, xd, yd, flags=flags)
+        torch.cuda.synchronize()
+        got = yd.cpu().numpy()
+        bad = np.nonzero(got.view(np.uint64) != expect.view(np.uint64))[0]
+        assert bad.size == 0, f"C={C} sigma={sigma}: rows {bad[:8]} (lengths {np.diff(A.rpt)[bad[:8]]})"
