@@ -73,7 +73,8 @@ namespace {
 void free_matrix(sell_matrix *h) {
     // every kernel that may still read the arrays must finish first
     (void)cudaDeviceSynchronize();
-    void *ptrs[] = {h->val, h->col, h->cs, h->cl, h->srl, h->perm, h->lchunk, h->xstage, h->ystage};
+    void *ptrs[] = {h->val,    h->col,   h->cs,   h->cl,     h->srl,    h->perm,
+                    h->lchunk, h->lunit, h->cnt, h->part, h->xstage, h->ystage};
     for (void *p : ptrs) h->al.put(p, nullptr);
     (void)cudaDeviceSynchronize();
     delete h;
@@ -242,7 +243,12 @@ sell_status sell_batch_create(const sell_batch_item *items, int32_t n, void *str
     if (!b) return fail(SELL_ENOMEM, "sell_batch_create: host allocation failed");
     sell_status st = batch_create(items, n, static_cast<cudaStream_t>(stream), b);
     if (st != SELL_OK) {
+        std::string msg = g_last_error;
+        (void)cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+        for (void *p : b->scratch) b->al.put(p, nullptr);
+        (void)cudaDeviceSynchronize();
         delete b;
+        g_last_error = msg;
         return st;
     }
     *out = b;
@@ -260,6 +266,7 @@ sell_status sell_batch_free(sell_batch_plan plan) {
     plan->al.put(plan->items, nullptr);
     plan->al.put(plan->units, nullptr);
     plan->al.put(plan->counter, nullptr);
+    for (void *p : plan->scratch) plan->al.put(p, nullptr);
     (void)cudaDeviceSynchronize();
     delete plan;
     return SELL_OK;

@@ -25,16 +25,19 @@ struct Prod {
     const int32_t *col;
     const int64_t *cs;
     const int32_t *srl;
-    const int32_t *cl;
     const int32_t *perm;
+    const int32_t *lchunk;
+    const int2 *lunit;
+    void *part;    // this product's own segment scratch (owned by the plan)
+    int32_t *cnt;  // this product's own segment counters (owned by the plan)
     const void *X;
     void *Y;
-    int64_t ldx, ldy, N;
+    int64_t ldx, ldy, N, long_threads;
     int32_t C, kb, type, acc, comp, vec;
 };
 
-// kind 0: a tile of kTileRows sorted rows starting at idx (its short rows);
-// kind 1: the long rows of chunk idx (one block, many threads per row).
+// kind 0: a tile of kTileRows sorted rows starting at row idx (short rows);
+// kind 1: kTileRows long-row work-unit threads starting at virtual thread idx.
 struct Unit {
     int32_t prod;
     int32_t kind;
@@ -42,15 +45,18 @@ struct Unit {
 };
 
 template <class VT, int K, class Acc>
-__device__ __noinline__ void do_unit(const Prod &P, const Unit &u, uint64_t pol, void *smem) {
+__device__ __noinline__ void do_unit(const Prod &P, const Unit &u, uint64_t pol) {
     using XT = typename XType<VT>::T;
     constexpr int U = K >= 8 ? 2 : (K >= 4 ? 4 : 8);
     const VT *val = static_cast<const VT *>(P.val);
     const XT *X = static_cast<const XT *>(P.X);
     XT *Y = static_cast<XT *>(P.Y);
     if (u.kind == 1) {
-        long_chunk<VT, XT, K, U, Acc>(val, P.col, P.cs, P.srl, P.cl, P.perm, X, P.ldx, Y, P.ldy, P.N, P.C,
-                                      u.idx, P.acc, P.vec != 0, pol, static_cast<Acc *>(smem));
+        const int64_t v = u.idx + threadIdx.x;
+        if (v < P.long_threads)
+            long_unit<VT, XT, K, U, Acc>(val, P.col, P.cs, P.srl, P.perm, P.lchunk, P.lunit,
+                                         static_cast<Acc *>(P.part), P.cnt, X, P.ldx, Y, P.ldy, P.N, P.C, v,
+                                         P.acc, P.vec != 0, pol);
     } else {
         const int64_t r = u.idx + threadIdx.x;
         if (r < P.N)
@@ -60,12 +66,12 @@ __device__ __noinline__ void do_unit(const Prod &P, const Unit &u, uint64_t pol,
 }
 
 template <class VT, class Acc>
-__device__ __forceinline__ void dispatch_k(const Prod &P, const Unit &u, uint64_t pol, void *smem) {
+__device__ __forceinline__ void dispatch_k(const Prod &P, const Unit &u, uint64_t pol) {
     switch (P.kb) {
-        case 1: do_unit<VT, 1, Acc>(P, u, pol, smem); break;
-        case 2: do_unit<VT, 2, Acc>(P, u, pol, smem); break;
-        case 4: do_unit<VT, 4, Acc>(P, u, pol, smem); break;
-        default: do_unit<VT, 8, Acc>(P, u, pol, smem); break;
+        case 1: do_unit<VT, 1, Acc>(P, u, pol); break;
+        case 2: do_unit<VT, 2, Acc>(P, u, pol); break;
+        case 4: do_unit<VT, 4, Acc>(P, u, pol); break;
+        default: do_unit<VT, 8, Acc>(P, u, pol); break;
     }
 }
 
@@ -73,7 +79,6 @@ __global__ void __launch_bounds__(kTileRows)
 k_batch(const Prod *__restrict__ prods, const Unit *__restrict__ units, int64_t nwork,
         unsigned int *counter) {
     __shared__ int64_t s_unit;
-    __shared__ __align__(16) unsigned char part[kTileRows * 8 * 8];  // block x K(8) x 8-byte Acc
     const uint64_t pol = l2_evict_first_policy();
     for (;;) {
         if (threadIdx.x == 0) s_unit = (int64_t)atomicAdd(counter, 1u);
@@ -84,13 +89,13 @@ k_batch(const Prod *__restrict__ prods, const Unit *__restrict__ units, int64_t 
         const Unit u = units[w];
         const Prod P = prods[u.prod];
         if (P.type == SELL_F64) {
-            dispatch_k<double, Plain<double>>(P, u, pol, part);
+            dispatch_k<double, Plain<double>>(P, u, pol);
         } else if (P.type == SELL_F32) {
-            if (P.comp) dispatch_k<float, Dot2>(P, u, pol, part);
-            else dispatch_k<float, Plain<float>>(P, u, pol, part);
+            if (P.comp) dispatch_k<float, Dot2>(P, u, pol);
+            else dispatch_k<float, Plain<float>>(P, u, pol);
         } else {
-            if (P.comp) dispatch_k<__nv_bfloat16, Dot2>(P, u, pol, part);
-            else dispatch_k<__nv_bfloat16, Plain<float>>(P, u, pol, part);
+            if (P.comp) dispatch_k<__nv_bfloat16, Dot2>(P, u, pol);
+            else dispatch_k<__nv_bfloat16, Plain<float>>(P, u, pol);
         }
         __syncthreads();
     }
@@ -122,7 +127,11 @@ sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s
             P.col = h->col;
             P.cs = h->cs;
             P.srl = h->srl;
-            P.cl = h->cl;
+            P.lchunk = h->lchunk;
+            P.lunit = h->lunit;
+            P.part = nullptr;
+            P.cnt = nullptr;
+            P.long_threads = h->nunits * h->C;
             P.perm = (h->flags & SELL_BUILD_PERMUTE_COLS) ? nullptr : h->perm;
             P.X = static_cast<const char *>(it.X) + done * xs;
             P.Y = static_cast<char *>(it.Y) + done * xs;
@@ -148,20 +157,31 @@ sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s
                      [](const std::pair<int64_t, int32_t> &a, const std::pair<int64_t, int32_t> &b) {
                          return a.first > b.first;
                      });
-    // long-row chunks first (they have the longest critical path), then row tiles
+    // each product with long rows gets its own segment scratch and counters,
+    // so products of one plan (even on the same matrix) never share them
+    b->al = current_allocator();
+    for (size_t i = 0; i < prods.size(); ++i) {
+        const sell_matrix *h = owner[i];
+        if (h->nunits == 0) continue;
+        void *p = b->al.get((size_t)h->nunits * h->C * prods[i].kb * 8, s);
+        void *c = p ? b->al.get((size_t)h->nlong * h->C * sizeof(int32_t), s) : nullptr;
+        if (p) b->scratch.push_back(p);
+        if (c) b->scratch.push_back(c);
+        if (!p || !c) return fail(SELL_ENOMEM, "sell_batch_create: segment scratch allocation failed");
+        SELL_CUDA_TRY(cudaMemsetAsync(c, 0, (size_t)h->nlong * h->C * sizeof(int32_t), s));
+        prods[i].part = p;
+        prods[i].cnt = static_cast<int32_t *>(c);
+    }
+    // long-row work first (its units are the longest), then row tiles
     std::vector<Unit> units;
     for (auto &o : order) {
-        const sell_matrix *h = owner[o.second];
-        if (h->nlong == 0) continue;
-        std::vector<int32_t> lc((size_t)h->nlong);
-        SELL_CUDA_TRY(cudaMemcpy(lc.data(), h->lchunk, h->nlong * sizeof(int32_t), cudaMemcpyDeviceToHost));
-        for (int32_t c : lc) units.push_back({o.second, 1, (int64_t)c});
+        const Prod &P = prods[o.second];
+        for (int64_t v0 = 0; v0 < P.long_threads; v0 += kTileRows) units.push_back({o.second, 1, v0});
     }
     for (auto &o : order) {
         const Prod &P = prods[o.second];
         for (int64_t r0 = 0; r0 < P.N; r0 += kTileRows) units.push_back({o.second, 0, r0});
     }
-    b->al = current_allocator();
     b->nprod = (int32_t)prods.size();
     b->nwork = (int64_t)units.size();
     DevBuf dp, du, dc;

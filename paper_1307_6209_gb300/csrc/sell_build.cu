@@ -333,6 +333,22 @@ __global__ void k_long_compact(const int32_t *__restrict__ cl, const int64_t *__
         if (cl[c] > kSeg) lchunk[pos[c]] = (int32_t)c;
 }
 
+// Long-row work units: chunk lc has ceil(cl / kSeg) segments; the units are
+// numbered chunk by chunk (ubase = exclusive scan of the segment counts).
+__global__ void k_long_nseg(const int32_t *__restrict__ cl, const int32_t *__restrict__ lchunk,
+                            int64_t nlong, int32_t *__restrict__ nseg) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nlong; i += stride)
+        nseg[i] = (cl[lchunk[i]] + kSeg - 1) / kSeg;
+}
+
+__global__ void k_long_units(const int32_t *__restrict__ nseg, const int64_t *__restrict__ ubase,
+                             int64_t nlong, int2 *__restrict__ lunit) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nlong; i += stride)
+        for (int32_t sg = 0; sg < nseg[i]; ++sg) lunit[ubase[i] + sg] = make_int2((int)i, sg);
+}
+
 // ------------------------------------------------------------------ scatter
 template <class TI, class TO> __device__ __forceinline__ TO cvt(TI v);
 template <> __device__ __forceinline__ double cvt<double, double>(double v) { return v; }
@@ -591,12 +607,29 @@ sell_status build_format(const sell_csr *A, const sell_opts *o, cudaStream_t s, 
         SELL_CUDA_TRY(cudaMemcpyAsync(&nlong, lpos.as<int64_t>() + Nc, sizeof(int64_t),
                                       cudaMemcpyDeviceToHost, s));
     SELL_CUDA_TRY(cudaStreamSynchronize(s));
-    DevBuf lchunk;
+    DevBuf lchunk, lnseg, lubase, lunit, cnt, part;
+    int64_t nunits = 0;
     if (nlong > 0) {
         SELL_TRY(lchunk.alloc(al, nlong * sizeof(int32_t), s));
         k_long_compact<<<grid_for(Nc, 256), 256, 0, s>>>(cl.as<int32_t>(), lpos.as<int64_t>(), Nc,
                                                          lchunk.as<int32_t>());
         SELL_CUDA_TRY(cudaGetLastError());
+        SELL_TRY(lnseg.alloc(al, nlong * sizeof(int32_t), s));
+        SELL_TRY(lubase.alloc(al, (nlong + 1) * sizeof(int64_t), s));
+        k_long_nseg<<<grid_for(nlong, 256), 256, 0, s>>>(cl.as<int32_t>(), lchunk.as<int32_t>(), nlong,
+                                                         lnseg.as<int32_t>());
+        SELL_CUDA_TRY(cudaGetLastError());
+        SELL_TRY(scan_exclusive<int32_t>(lnseg.as<int32_t>(), 1, nlong, lubase.as<int64_t>(), al, s));
+        SELL_CUDA_TRY(cudaMemcpyAsync(&nunits, lubase.as<int64_t>() + nlong, sizeof(int64_t),
+                                      cudaMemcpyDeviceToHost, s));
+        SELL_CUDA_TRY(cudaStreamSynchronize(s));
+        SELL_TRY(lunit.alloc(al, nunits * sizeof(int2), s));
+        k_long_units<<<grid_for(nlong, 256), 256, 0, s>>>(lnseg.as<int32_t>(), lubase.as<int64_t>(), nlong,
+                                                          lunit.as<int2>());
+        SELL_CUDA_TRY(cudaGetLastError());
+        SELL_TRY(cnt.alloc(al, nlong * C * sizeof(int32_t), s));
+        SELL_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, nlong * C * sizeof(int32_t), s));
+        SELL_TRY(part.alloc(al, (size_t)nunits * C * 8, s));
     }
 
     // 6. values and columns
@@ -639,8 +672,14 @@ sell_status build_format(const sell_csr *A, const sell_opts *o, cudaStream_t s, 
     }
     h->al = al;
     h->nlong = nlong;
-    h->device_bytes = val.bytes + col.bytes + cs.bytes + cl.bytes + srl.bytes + perm.bytes + lchunk.bytes;
+    h->nunits = nunits;
+    h->part_k = nunits > 0 ? 1 : 0;
+    h->device_bytes = val.bytes + col.bytes + cs.bytes + cl.bytes + srl.bytes + perm.bytes + lchunk.bytes +
+                      lunit.bytes + cnt.bytes + part.bytes;
     h->lchunk = (int32_t *)lchunk.release_ownership();
+    h->lunit = (int2 *)lunit.release_ownership();
+    h->cnt = (int32_t *)cnt.release_ownership();
+    h->part = part.release_ownership();
     h->val = val.release_ownership();
     h->col = (int32_t *)col.release_ownership();
     h->cs = (int64_t *)cs.release_ownership();

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "sell.h"
 
@@ -81,6 +82,11 @@ struct sell_matrix {
     int32_t *perm = nullptr;   // nrows, sorted -> original (null: identity)
     int32_t *lchunk = nullptr; // nlong chunks holding rows longer than kSeg
     int64_t nlong = 0;
+    int2 *lunit = nullptr;     // nunits long-row work units {long chunk, segment}
+    int64_t nunits = 0;
+    int32_t *cnt = nullptr;    // nlong * C per-row segment counters (zero at rest)
+    void *part = nullptr;      // segment partials: nunits * C * part_k * 8 bytes
+    int32_t part_k = 0;
     // host-io staging (lazily allocated)
     void *xstage = nullptr, *ystage = nullptr;
     size_t xstage_bytes = 0, ystage_bytes = 0;
@@ -90,6 +96,7 @@ struct sell_matrix {
 struct sell_batch {
     int device = 0;
     sell::Allocator al;
+    std::vector<void *> scratch;  // per-product segment scratch and counters
     void *items = nullptr;      // device product table
     void *units = nullptr;      // device work-unit table
     unsigned int *counter = nullptr;
@@ -102,7 +109,7 @@ namespace sell {
 
 // --------------------------------------------------------- launch entry points
 // (defined in sell_spmv.cu / sell_build.cu / sell_batch.cu / sell_bench.cu)
-sell_status launch_spmmv(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy,
+sell_status launch_spmmv(sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy,
                          int32_t k, uint32_t flags, cudaStream_t s);
 sell_status build_format(const sell_csr *A, const sell_opts *o, cudaStream_t s, sell_matrix *h);
 sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s, sell_batch *b);

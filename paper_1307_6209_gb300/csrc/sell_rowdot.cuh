@@ -11,9 +11,14 @@
 //               segment 0 is a chain starting at y0, every other segment a
 //               chain starting at 0; the segment results are then added in
 //               segment order (Dot2: merged with TwoSum, errors carried).
-// The segments let one block work on a long chunk with many threads at once
-// (Sec. 3.4 notes that one thread per row leaves a warp waiting for its
-// longest row; Sec. 5.2 suggests several threads per row for such rows).
+// Every segment of a long row is an independent work unit, so long rows are
+// spread over the whole grid instead of holding one warp for their full
+// length (Sec. 3.4 notes that one thread per row leaves a warp waiting for
+// its longest row; Sec. 5.2 suggests several threads per row for such rows).
+// A segment's partial result goes to scratch memory; the thread that
+// completes the last segment of a row (per-row counter) folds the partials
+// in segment order, so the result does not depend on which segment finished
+// last.
 #pragma once
 
 #include "sell_internal.cuh"
@@ -36,6 +41,11 @@ struct Plain {
     __device__ __forceinline__ void add(AT a, AT b) { s = fma(a, b, s); }
     __device__ __forceinline__ void merge(const Plain &o) { s = s + o.s; }
     __device__ __forceinline__ AT result() const { return s; }
+    __device__ __forceinline__ static Plain load_l2(const Plain *p) {
+        Plain r;
+        r.s = __ldcg(&p->s);
+        return r;
+    }
 };
 
 // Dot2 (Ogita, Rump, Oishi 2005): p is the running sum, e the sum of the
@@ -64,6 +74,13 @@ struct Dot2 {
         e = __fadd_rn(e, __fadd_rn(q, o.e));
     }
     __device__ __forceinline__ float result() const { return __fadd_rn(p, e); }
+    __device__ __forceinline__ static Dot2 load_l2(const Dot2 *q) {
+        float2 t = __ldcg(reinterpret_cast<const float2 *>(q));
+        Dot2 r;
+        r.p = t.x;
+        r.e = t.y;
+        return r;
+    }
 };
 
 // K consecutive right-hand-side values of row `ci` of X (row-major, ldx).
@@ -101,9 +118,9 @@ __device__ __forceinline__ void load_x(const XT *__restrict__ X, int64_t ldx, in
 }
 
 // One chain over entries j0..j1-1 of a row whose entry j sits at vp[j*C]
-// (values) and cp[j*C] (columns).  U entries are loaded per step, predicated
-// on j < j1, so that short rows still keep U loads in flight; the FMAs are
-// applied in entry order.
+// (values) and cp[j*C] (columns), in entry order.  Full groups of U entries
+// are loaded before their gathers and FMAs; the last, partial group is loaded
+// with predicates so that short rows keep all their loads in flight.
 template <class VT, class XT, int K, int U, class Acc>
 __device__ __forceinline__ void chain(Acc (&acc)[K], const VT *__restrict__ vp,
                                       const int32_t *__restrict__ cp, int C, int j0, int j1,
@@ -111,94 +128,102 @@ __device__ __forceinline__ void chain(Acc (&acc)[K], const VT *__restrict__ vp,
     const int64_t stride = C;
     vp += (int64_t)j0 * stride;
     cp += (int64_t)j0 * stride;
-    for (int j = j0; j < j1; j += U) {
+    int j = j0;
+    for (; j + U <= j1; j += U) {
         VT v[U];
         int32_t ci[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            if (j + u < j1) {
-                v[u] = ld_stream(vp + u * stride, pol);
-                ci[u] = ld_stream(cp + u * stride, pol);
-            }
+            v[u] = ld_stream(vp + u * stride, pol);
+            ci[u] = ld_stream(cp + u * stride, pol);
         }
         XT xv[U][K];
 #pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (j + u < j1) load_x<K>(X, ldx, ci[u], vec, xv[u]);
+        for (int u = 0; u < U; ++u) load_x<K>(X, ldx, ci[u], vec, xv[u]);
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            if (j + u < j1) {
-                XT a = widen(v[u]);
+            XT a = widen(v[u]);
 #pragma unroll
-                for (int q = 0; q < K; ++q) acc[q].add(a, xv[u][q]);
-            }
+            for (int q = 0; q < K; ++q) acc[q].add(a, xv[u][q]);
         }
         vp += U * stride;
         cp += U * stride;
     }
-}
-
-// A block works on the long rows (L > kSeg) of chunk c.  Lp = min(C, block)
-// lanes form a group; the G = block / Lp groups take segments g, g+G, ...;
-// after every round the partial results go through shared memory and the
-// first group folds them in segment order.  `part` holds block * K Accs.
-template <class VT, class XT, int K, int U, class Acc>
-__device__ __forceinline__ void long_chunk(const VT *__restrict__ val, const int32_t *__restrict__ col,
-                                           const int64_t *__restrict__ cs, const int32_t *__restrict__ srl,
-                                           const int32_t *__restrict__ cl, const int32_t *__restrict__ perm,
-                                           const XT *__restrict__ X, int64_t ldx, XT *Y, int64_t ldy,
-                                           int64_t N, int C, int64_t c, int accumulate, bool vec,
-                                           uint64_t pol, Acc *part) {
-    const int B = blockDim.x;
-    const int Lp = C < B ? C : B;
-    const int G = B / Lp;
-    const int g = threadIdx.x / Lp;
-    const int l0 = threadIdx.x - g * Lp;
-    const int nseg_max = (cl[c] + kSeg - 1) / kSeg;
-    const int rounds = (nseg_max + G - 1) / G;
-    const int64_t base = cs[c];
-    for (int lb = 0; lb < C; lb += Lp) {
-        const int l = lb + l0;
-        const int64_t r = c * C + l;
-        const bool in = g < G && l < C && r < N;
-        const int L = in ? srl[r] : 0;
-        const bool active = in && L > kSeg;
-        const int nseg = active ? (L + kSeg - 1) / kSeg : 0;
-        const int64_t out = active ? (perm ? (int64_t)perm[r] : r) : 0;
-        Acc tot[K];
-        for (int k = 0; k < rounds; ++k) {
-            const int s = k * G + g;
-            if (active && s < nseg) {
-                Acc acc[K];
+    if constexpr (U > 1) {
+        if (j < j1) {
+            VT v[U];
+            int32_t ci[U];
 #pragma unroll
-                for (int q = 0; q < K; ++q)
-                    acc[q].init((s == 0 && accumulate) ? Y[out * ldy + q] : XT(0));
-                const int j0 = s * kSeg;
-                const int j1 = min(L, j0 + kSeg);
-                chain<VT, XT, K, U, Acc>(acc, val + base + l, col + base + l, C, j0, j1, X, ldx, vec, pol);
-#pragma unroll
-                for (int q = 0; q < K; ++q) part[threadIdx.x * K + q] = acc[q];
-            }
-            __syncthreads();
-            if (g == 0 && active) {
-                for (int gg = 0; gg < G; ++gg) {
-                    const int s2 = k * G + gg;
-                    if (s2 >= nseg) break;
-#pragma unroll
-                    for (int q = 0; q < K; ++q) {
-                        const Acc &p = part[(gg * Lp + l0) * K + q];
-                        if (s2 == 0) tot[q] = p;
-                        else tot[q].merge(p);
-                    }
+            for (int u = 0; u < U - 1; ++u) {
+                if (j + u < j1) {
+                    v[u] = ld_stream(vp + u * stride, pol);
+                    ci[u] = ld_stream(cp + u * stride, pol);
                 }
             }
-            __syncthreads();
-        }
-        if (g == 0 && active) {
+            XT xv[U][K];
 #pragma unroll
-            for (int q = 0; q < K; ++q) Y[out * ldy + q] = tot[q].result();
+            for (int u = 0; u < U - 1; ++u)
+                if (j + u < j1) load_x<K>(X, ldx, ci[u], vec, xv[u]);
+#pragma unroll
+            for (int u = 0; u < U - 1; ++u) {
+                if (j + u < j1) {
+                    XT a = widen(v[u]);
+#pragma unroll
+                    for (int q = 0; q < K; ++q) acc[q].add(a, xv[u][q]);
+                }
+            }
         }
     }
+}
+
+// One thread of a long-row work unit.  Units are (long chunk lc, segment s)
+// pairs, numbered chunk by chunk (lunit[u] = {lc, s}); a unit has C threads,
+// virtual thread v = u*C + l takes lane l.  part holds K Accs per (unit,
+// lane); cnt one counter per (long chunk, lane), zero between products.
+template <class VT, class XT, int K, int U, class Acc>
+__device__ __forceinline__ void long_unit(const VT *__restrict__ val, const int32_t *__restrict__ col,
+                                          const int64_t *__restrict__ cs, const int32_t *__restrict__ srl,
+                                          const int32_t *__restrict__ perm, const int32_t *__restrict__ lchunk,
+                                          const int2 *__restrict__ lunit, Acc *part, int32_t *cnt,
+                                          const XT *__restrict__ X, int64_t ldx, XT *Y, int64_t ldy,
+                                          int64_t N, int C, int64_t v, int accumulate, bool vec,
+                                          uint64_t pol) {
+    const int64_t u = v / C;
+    const int l = (int)(v - u * C);
+    const int2 us = lunit[u];
+    const int64_t c = lchunk[us.x];
+    const int64_t r = c * C + l;
+    if (r >= N) return;
+    const int L = srl[r];
+    if (L <= kSeg) return;  // short rows belong to the per-row path
+    const int nseg = (L + kSeg - 1) / kSeg;
+    const int s = us.y;
+    if (s >= nseg) return;
+    const int64_t out = perm ? (int64_t)perm[r] : r;
+    Acc acc[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) acc[q].init((s == 0 && accumulate) ? Y[out * ldy + q] : XT(0));
+    const int64_t base = cs[c] + l;
+    chain<VT, XT, K, U, Acc>(acc, val + base, col + base, C, s * kSeg, min(L, (s + 1) * kSeg), X, ldx, vec,
+                             pol);
+#pragma unroll
+    for (int q = 0; q < K; ++q) part[(u * C + l) * K + q] = acc[q];
+    __threadfence();
+    int32_t *ct = cnt + (int64_t)us.x * C + l;
+    if (atomicAdd(ct, 1) != nseg - 1) return;
+    // this thread completed the row: fold the segments in order
+    __threadfence();
+    const int64_t u0 = u - s;
+    Acc tot[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) tot[q] = Acc::load_l2(part + (u0 * C + l) * K + q);
+    for (int s2 = 1; s2 < nseg; ++s2) {
+#pragma unroll
+        for (int q = 0; q < K; ++q) tot[q].merge(Acc::load_l2(part + ((u0 + s2) * C + l) * K + q));
+    }
+#pragma unroll
+    for (int q = 0; q < K; ++q) Y[out * ldy + q] = tot[q].result();
+    *ct = 0;
 }
 
 // The thread's own row when it is short (L <= kSeg); long rows return.

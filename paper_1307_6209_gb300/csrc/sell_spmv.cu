@@ -22,19 +22,20 @@ namespace {
 template <class VT, int K, int U, class Acc>
 __global__ void __launch_bounds__(512)
 k_spmmv(const VT *__restrict__ val, const int32_t *__restrict__ col, const int64_t *__restrict__ cs,
-        const int32_t *__restrict__ srl, const int32_t *__restrict__ cl, const int32_t *__restrict__ perm,
-        const int32_t *__restrict__ lchunk, int64_t nlong, const typename XType<VT>::T *__restrict__ X,
-        int64_t ldx, typename XType<VT>::T *Y, int64_t ldy, int64_t N, int C, int accumulate, int vec) {
+        const int32_t *__restrict__ srl, const int32_t *__restrict__ perm, const int32_t *__restrict__ lchunk,
+        const int2 *__restrict__ lunit, int64_t long_threads, int64_t long_blocks, Acc *part, int32_t *cnt,
+        const typename XType<VT>::T *__restrict__ X, int64_t ldx, typename XType<VT>::T *Y, int64_t ldy,
+        int64_t N, int C, int accumulate, int vec) {
     using XT = typename XType<VT>::T;
     const uint64_t pol = l2_evict_first_policy();
-    if (blockIdx.x < nlong) {
-        extern __shared__ __align__(16) unsigned char smem_raw[];
-        long_chunk<VT, XT, K, U, Acc>(val, col, cs, srl, cl, perm, X, ldx, Y, ldy, N, C,
-                                      (int64_t)lchunk[blockIdx.x], accumulate, vec != 0, pol,
-                                      reinterpret_cast<Acc *>(smem_raw));
+    if (blockIdx.x < long_blocks) {
+        const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        if (v < long_threads)
+            long_unit<VT, XT, K, U, Acc>(val, col, cs, srl, perm, lchunk, lunit, part, cnt, X, ldx, Y, ldy, N, C,
+                                         v, accumulate, vec != 0, pol);
         return;
     }
-    const int64_t r = (blockIdx.x - nlong) * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t r = (blockIdx.x - long_blocks) * (int64_t)blockDim.x + threadIdx.x;
     if (r >= N) return;
     short_row<VT, XT, K, U, Acc>(val, col, cs, srl, perm, X, ldx, Y, ldy, C, r, accumulate, vec != 0, pol);
 }
@@ -43,17 +44,14 @@ template <class VT, int K, int U, class Acc>
 cudaError_t run(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy, int acc,
                 int vec, cudaStream_t s) {
     using XT = typename XType<VT>::T;
-    const int64_t grid = h->nlong + (h->nrows + h->block - 1) / h->block;
-    const size_t smem = h->nlong ? (size_t)h->block * K * sizeof(Acc) : 0;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_spmmv<VT, K, U, Acc>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    k_spmmv<VT, K, U, Acc><<<(unsigned)grid, h->block, smem, s>>>(
-        static_cast<const VT *>(h->val), h->col, h->cs, h->srl, h->cl,
-        (h->flags & SELL_BUILD_PERMUTE_COLS) ? nullptr : h->perm, h->lchunk, h->nlong,
-        static_cast<const XT *>(X), ldx, static_cast<XT *>(Y), ldy, h->nrows, h->C, acc, vec);
+    const int64_t long_threads = h->nunits * h->C;
+    const int64_t long_blocks = (long_threads + h->block - 1) / h->block;
+    const int64_t grid = long_blocks + (h->nrows + h->block - 1) / h->block;
+    k_spmmv<VT, K, U, Acc><<<(unsigned)grid, h->block, 0, s>>>(
+        static_cast<const VT *>(h->val), h->col, h->cs, h->srl,
+        (h->flags & SELL_BUILD_PERMUTE_COLS) ? nullptr : h->perm, h->lchunk, h->lunit, long_threads,
+        long_blocks, static_cast<Acc *>(h->part), h->cnt, static_cast<const XT *>(X), ldx,
+        static_cast<XT *>(Y), ldy, h->nrows, h->C, acc, vec);
     return cudaGetLastError();
 }
 
@@ -92,9 +90,20 @@ cudaError_t pick_k(const sell_matrix *h, const void *X, int64_t ldx, void *Y, in
 
 // Splits k into kernel blocks of 8, 4, 2, 1 columns (every column keeps the
 // same per-row operation order, so the split does not change any result).
-sell_status launch_spmmv(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy,
+// The segment scratch grows on the first product with a wider block.
+sell_status launch_spmmv(sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy,
                          int32_t k, uint32_t flags, cudaStream_t s) {
     if (h->nrows == 0) return SELL_OK;
+    if (h->nunits > 0) {
+        const int need = k >= 8 ? 8 : k >= 4 ? 4 : k >= 2 ? 2 : 1;
+        if (need > h->part_k) {
+            void *p = h->al.get((size_t)h->nunits * h->C * need * 8, s);
+            if (!p) return fail(SELL_ENOMEM, "segment scratch allocation failed");
+            h->al.put(h->part, s);
+            h->part = p;
+            h->part_k = need;
+        }
+    }
     const int acc = (flags & SELL_SPMV_ACCUMULATE) ? 1 : 0;
     const bool comp = (flags & SELL_SPMV_COMPENSATED) != 0;
     const size_t xs = h->store_type == SELL_F64 ? 8 : 4;
