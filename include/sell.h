@@ -170,6 +170,31 @@ SELL_API sell_status sell_spmv(sell_handle h, const void *x, void *y, uint32_t f
 SELL_API sell_status sell_spmmv(sell_handle h, const void *X, int64_t ldx, void *Y, int64_t ldy,
                        int32_t k, uint32_t flags, void *stream);
 
+/* The product of sell_spmmv without allocating any memory.  The paper has no
+ * counterpart; this entry point is for callers that cannot allocate device
+ * memory at the time they multiply -- a serving loop held to a fixed memory
+ * budget, code running inside another framework's memory pool, or a
+ * latency-critical path that must not wait for an allocation.  (sell_spmmv
+ * itself may allocate: staging buffers for SELL_SPMV_HOST_IO, and a larger
+ * long-row scratch the first time a call uses more right-hand sides.)
+ * Instead of memory owned by the handle, the partial sums of long rows
+ * (rows longer than 64 entries) go to one fixed 4 MiB device array that the
+ * library holds on every device where it is loaded, until the process exits.
+ * Arguments and results are those of sell_spmmv, bit for bit; X and Y are
+ * device buffers (SELL_SPMV_HOST_IO is rejected).  The right-hand sides are
+ * processed in blocks of up to 8 columns, narrower if the array is too small
+ * for 8.  Errors: SELL_EINVAL when even one column's long-row scratch exceeds
+ * 4 MiB (the message states the need), plus those of sell_spmmv.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call shares the one array and leaves its
+ * contents behind (the counters are cleared at the start of every call): two
+ * calls whose work overlaps on the GPU -- on different streams, or from
+ * different threads -- race and give wrong results.  Calls issued on one
+ * stream are ordered and safe. */
+SELL_API sell_status sell_spmmv_noalloc(sell_handle h, const void *X, int64_t ldx, void *Y, int64_t ldy,
+                                        int32_t k, uint32_t flags, void *stream);
+
 /* Launch tuning of a handle's SpMV/SpMMV kernels (autotuner knob):
  * block = threads per block (32..512, multiple of 32), unroll = independent
  * loads in flight per thread (1, 2, 4 or 8).  0 keeps the current value. */

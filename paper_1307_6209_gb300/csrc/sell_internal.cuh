@@ -111,6 +111,9 @@ namespace sell {
 // (defined in sell_spmv.cu / sell_build.cu / sell_batch.cu / sell_bench.cu)
 sell_status launch_spmmv(sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy,
                          int32_t k, uint32_t flags, cudaStream_t s);
+sell_status launch_block_with_scratch(const sell_matrix *h, const void *X, int64_t ldx, void *Y,
+                                      int64_t ldy, int kb, uint32_t flags, void *part, int32_t *cnt,
+                                      cudaStream_t s);
 sell_status build_format(const sell_csr *A, const sell_opts *o, cudaStream_t s, sell_matrix *h);
 sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s, sell_batch *b);
 sell_status batch_run(const sell_batch *b, int32_t grid, cudaStream_t s);

@@ -55,6 +55,33 @@ cudaError_t run(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64
     return cudaGetLastError();
 }
 
+// Same launch with caller-chosen segment scratch (used by sell_spmmv_noalloc).
+template <class VT, int K, int U, class Acc>
+cudaError_t run_with(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy, int acc,
+                     int vec, void *part, int32_t *cnt, cudaStream_t s) {
+    using XT = typename XType<VT>::T;
+    const int64_t long_threads = h->nunits * h->C;
+    const int64_t long_blocks = (long_threads + h->block - 1) / h->block;
+    const int64_t grid = long_blocks + (h->nrows + h->block - 1) / h->block;
+    k_spmmv<VT, K, U, Acc><<<(unsigned)grid, h->block, 0, s>>>(
+        static_cast<const VT *>(h->val), h->col, h->cs, h->srl,
+        (h->flags & SELL_BUILD_PERMUTE_COLS) ? nullptr : h->perm, h->lchunk, h->lunit, long_threads,
+        long_blocks, static_cast<Acc *>(part), cnt, static_cast<const XT *>(X), ldx, static_cast<XT *>(Y),
+        ldy, h->nrows, h->C, acc, vec);
+    return cudaGetLastError();
+}
+
+template <class VT, class Acc>
+cudaError_t pick_with(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy, int kb,
+                      int acc, int vec, void *part, int32_t *cnt, cudaStream_t s) {
+    switch (kb) {
+        case 1: return run_with<VT, 1, 4, Acc>(h, X, ldx, Y, ldy, acc, vec, part, cnt, s);
+        case 2: return run_with<VT, 2, 4, Acc>(h, X, ldx, Y, ldy, acc, vec, part, cnt, s);
+        case 4: return run_with<VT, 4, 2, Acc>(h, X, ldx, Y, ldy, acc, vec, part, cnt, s);
+        default: return run_with<VT, 8, 2, Acc>(h, X, ldx, Y, ldy, acc, vec, part, cnt, s);
+    }
+}
+
 // Unroll choices keep U * K <= 16 gathered values per thread.
 template <class VT, int K, class Acc>
 cudaError_t pick_unroll(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy,
@@ -131,6 +158,33 @@ sell_status launch_spmmv(sell_matrix *h, const void *X, int64_t ldx, void *Y, in
         if (e != cudaSuccess) return cuda_fail(e, "SpMV kernel launch");
         done += kb;
     }
+    return SELL_OK;
+}
+
+// One column block of up to 8 right-hand sides with the given segment scratch
+// `part` (nunits * C * kb * 8 bytes) and zeroed counters `cnt` (nlong * C).
+sell_status launch_block_with_scratch(const sell_matrix *h, const void *X, int64_t ldx, void *Y,
+                                      int64_t ldy, int kb, uint32_t flags, void *part, int32_t *cnt,
+                                      cudaStream_t s) {
+    const int acc = (flags & SELL_SPMV_ACCUMULATE) ? 1 : 0;
+    const bool comp = (flags & SELL_SPMV_COMPENSATED) != 0;
+    const size_t xs = h->store_type == SELL_F64 ? 8 : 4;
+    const int vec = (((uintptr_t)X % 16) == 0 && ((ldx * xs) % 16) == 0) ? 1 : 0;
+    cudaError_t e;
+    switch (h->store_type) {
+        case SELL_F64:
+            e = pick_with<double, Plain<double>>(h, X, ldx, Y, ldy, kb, acc, vec, part, cnt, s);
+            break;
+        case SELL_F32:
+            e = comp ? pick_with<float, Dot2>(h, X, ldx, Y, ldy, kb, acc, vec, part, cnt, s)
+                     : pick_with<float, Plain<float>>(h, X, ldx, Y, ldy, kb, acc, vec, part, cnt, s);
+            break;
+        default:
+            e = comp ? pick_with<__nv_bfloat16, Dot2>(h, X, ldx, Y, ldy, kb, acc, vec, part, cnt, s)
+                     : pick_with<__nv_bfloat16, Plain<float>>(h, X, ldx, Y, ldy, kb, acc, vec, part, cnt, s);
+            break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "SpMV kernel launch");
     return SELL_OK;
 }
 

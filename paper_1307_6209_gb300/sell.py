@@ -73,6 +73,8 @@ SIGNATURES = {
     "sell_spmv": (ctypes.c_int, [_P, _P, _P, ctypes.c_uint32, _P]),
     "sell_spmmv": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32,
                                   ctypes.c_uint32, _P]),
+    "sell_spmmv_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32,
+                                          ctypes.c_uint32, _P]),
     "sell_set_launch": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     "sell_info": (ctypes.c_int, [_P, ctypes.POINTER(sell_info_t)]),
     "sell_export": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
@@ -223,6 +225,17 @@ def sell_spmmv(h: SellMatrix, X, Y, flags: int = 0, stream=None, ldx=None, ldy=N
     ldy = int(Y.stride(0) if hasattr(Y, "stride") and callable(Y.stride) else Y.strides[0] // Y.itemsize) \
         if ldy is None else int(ldy)
     _check(load().sell_spmmv(h.handle, _ptr(X), ldx, _ptr(Y), ldy, k, int(flags), _stream_ptr(stream)))
+    return Y
+
+
+def sell_spmmv_noalloc(h: SellMatrix, X, Y, flags: int = 0, stream=None):
+    """Y = A X like sell_spmmv, allocating nothing (long-row scratch in the
+    library's fixed 4 MiB device array; see include/sell.h)."""
+    if X.dim() == 1:
+        k, ldx, ldy = 1, 1, 1
+    else:
+        k, ldx, ldy = int(X.shape[1]), int(X.stride(0)), int(Y.stride(0))
+    _check(load().sell_spmmv_noalloc(h.handle, _ptr(X), ldx, _ptr(Y), ldy, k, int(flags), _stream_ptr(stream)))
     return Y
 
 
