@@ -3,9 +3,13 @@
 
 Default workload: random square matrix, N = 2,000,000 rows, row lengths
 lognormal (mean 16, log-sd 1.2, capped at 2000), uniform distinct columns,
-N(0,1) binary64 values, x ~ U[-1, 1] (seed 0).  The format is built once for
-every point of the sweep C in {32, 64, 128} x sigma in {1, 256, 4096, N};
-the headline step is one binary64 SpMV y = A x at the fastest point.
+N(0,1) binary64 values, x ~ U[-1, 1] (seed 0).  The autotuner builds the
+format for every point of the sweep C in {32, 64, 128} x sigma in
+{1, 256, 4096, N}, then picks the launch shape; the headline step is one
+binary64 SpMV y = A x with the tuned choice.  The line also reports SpMMV,
+binary32/bfloat16 storage, the end-to-end rate through host buffers, the
+co-bounds (HBM read bandwidth, L2 random-gather rate, FP64 FMA rate), and the
+27-point stencil on 200^3 in binary64/binary32/bfloat16.
 
 One JSON line is printed by rank 0.  Under torchrun every rank runs its own
 replica of the workload on its own GPU (independent problems, no data-path
@@ -199,17 +203,18 @@ def time_spmmv(sell, h, Xd, Yd, stream, reps, warm=3, flags=0):
 
 
 def measure_read_bw(sell, stream, nbytes=4 * 2 ** 30, reps=10):
+    """Best-of-reps bandwidth of the read-only kernel (Listing "reduction"
+    analogue) over a buffer far larger than L2."""
     import torch
-    buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
-    buf.fill_(1)
-    sink = torch.empty(152 * 8, dtype=torch.float64, device="cuda")
-    for _ in range(2):
-        sell.sell_bench_read(buf, nbytes, sink, grid=152 * 4, stream=stream)
+    buf = torch.ones(nbytes // 4, dtype=torch.int32, device="cuda")
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    sink = torch.empty(sms * 16, dtype=torch.float64, device="cuda")
+    sell.sell_bench_read(buf, nbytes, sink, grid=0, stream=stream)
     best = 1e30
     for _ in range(reps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        sell.sell_bench_read(buf, nbytes, sink, grid=152 * 4, stream=stream)
+        sell.sell_bench_read(buf, nbytes, sink, grid=0, stream=stream)
         b.record(stream)
         b.synchronize()
         best = min(best, a.elapsed_time(b) * 1e-3)
@@ -217,9 +222,29 @@ def measure_read_bw(sell, stream, nbytes=4 * 2 ** 30, reps=10):
     return nbytes / best / 1e9
 
 
+def measure_gather(sell, stream, n_words, reps=5, iters=64):
+    """Random 8-byte gathers per second from an n_words array (L2-resident
+    when n_words * 8 is well below the 129 MB L2)."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    grid = sms * 8
+    x = torch.ones(n_words, dtype=torch.int64, device="cuda")
+    sink = torch.empty(grid * 256, dtype=torch.float64, device="cuda")
+    sell.sell_bench_gather(x, n_words, sink, grid, iters, stream=stream)
+    best = 1e30
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sell.sell_bench_gather(x, n_words, sink, grid, iters, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        best = min(best, a.elapsed_time(b) * 1e-3)
+    return grid * 256 * iters * 8 / best / 1e9
+
+
 def measure_fp64_fma(sell, stream, iters=2000):
     import torch
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     grid = sms * 8
     sink = torch.empty(grid * 256, dtype=torch.float64, device="cuda")
     sell.sell_bench_fma64(sink, grid, 10, stream=stream)
@@ -292,8 +317,63 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ our arm
+def tune_launch(sell, h, xd, yd, stream, flags=0, blocks=(128, 256), unrolls=(1, 2, 4)):
+    """Pick (block, unroll) for one handle by timing; returns (block, unroll, seconds)."""
+    best = None
+    for b in blocks:
+        for u in unrolls:
+            sell.sell_set_launch(h, b, u)
+            dt = time_spmv(sell, h, xd, yd, stream, reps=30, flags=flags)
+            if best is None or dt < best[2]:
+                best = (b, u, dt)
+    sell.sell_set_launch(h, best[0], best[1])
+    return best
+
+
+def stencil_section(sell, model, stream, peak, fma_tf, n=200):
+    """27-point stencil on n^3 (generated on the device): binary64, binary32 and
+    bfloat16 storage, each with its tuned launch."""
+    import torch
+    from paper_1307_6209_gb300 import synth
+    A = synth.stencil27_device(n, perturb=0.1, seed=0)
+    x = torch.rand(A.ncols, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(0)) * 2 - 1
+    out = {"workload": f"27-point stencil {n}^3, N={A.nrows}, nnz={A.nnz}, SELL-32-1", "nnz": A.nnz}
+    y64 = None
+    for name, st in (("f64", sell.SELL_F64), ("f32", sell.SELL_F32), ("bf16", sell.SELL_BF16)):
+        t0 = time.perf_counter()
+        h = sell.sell_build(A, C=32, sigma=1, store_type=st, stream=stream)
+        bms = (time.perf_counter() - t0) * 1e3
+        xs = x if st == sell.SELL_F64 else x.float()
+        ys = torch.empty(A.nrows, dtype=xs.dtype, device="cuda")
+        blk, unr, _ = tune_launch(sell, h, xs, ys, stream)
+        dt = time_spmv(sell, h, xs, ys, stream, reps=200)
+        torch.cuda.synchronize()
+        vb = 8 if st == sell.SELL_F64 else (4 if st == sell.SELL_F32 else 2)
+        xb = 8 if st == sell.SELL_F64 else 4
+        alg = model.algorithmic_bytes(A.nrows, A.ncols, A.nnz, h.info.nchunks, 32, vb, xb, False)
+        row = {"us": round(dt * 1e6, 2), "gflops": round(2.0 * A.nnz / dt / 1e9, 1),
+               "gbs": round(alg / dt / 1e9, 1), "hbm_frac": round(alg / dt / 1e9 / peak, 4),
+               "block": blk, "unroll": unr, "build_ms": round(bms, 1), "beta": round(h.info.beta, 6)}
+        if st == sell.SELL_F64:
+            y64 = ys.clone()
+            if fma_tf:
+                row["fp64_pipe_frac"] = round(2.0 * A.nnz / dt / 1e12 / fma_tf, 4)
+            t64 = dt
+        else:
+            err = (ys.double() - y64).abs()
+            row["speedup_vs_f64"] = round(t64 / dt, 3)
+            row["max_abs_err_vs_f64"] = float(err.max())
+            row["rel_err_vs_f64"] = float(err.norm() / y64.norm())
+        out[name] = row
+        h.free()
+    del A
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
+    from paper_1307_6209_gb300 import autotune
     from paper_1307_6209_gb300 import build as cuda_build
     from paper_1307_6209_gb300 import model, sell
 
@@ -309,6 +389,7 @@ def run_ours(args):
     A, x, desc, grid = make_workload(args)
     n_gpus = ws
     dev_name = torch.cuda.get_device_name(local)
+    peak, peak_src = load_peaks()
 
     with torch.cuda.stream(stream):
         xd = torch.from_numpy(x).cuda()
@@ -317,31 +398,27 @@ def run_ours(args):
                         torch.from_numpy(A.val).cuda())
         torch.cuda.synchronize()
 
-        # ---- sweep of (C, sigma): build once each, time 50 SpMVs
-        sweep = []
-        if args.C is not None or args.sigma is not None or args.no_sweep:
-            grid = [(args.C or 32, args.sigma or 1)]
-        best = None
-        for C, sigma in grid:
-            t0 = time.perf_counter()
-            h = sell.sell_build(csr_d, C=C, sigma=sigma, stream=stream)
-            build_ms = (time.perf_counter() - t0) * 1e3
-            dt = time_spmv(sell, h, xd, yd, stream, reps=50)
-            gf = 2.0 * A.nnz / dt / 1e9
-            sweep.append({"C": C, "sigma": sigma, "beta": round(h.info.beta, 4), "gflops": round(gf, 1),
-                          "us": round(dt * 1e6, 2), "build_ms": round(build_ms, 2)})
-            if best is None or gf > best[0]:
-                if best is not None:
-                    best[1].free()
-                best = (gf, h, C, sigma, build_ms)
-            else:
-                h.free()
-        _, h, C, sigma, build_ms = best
-        inf = h.info
+        # ---- measuring kernels: read bandwidth b, random-gather rate, FP64 FMA peak
+        b_read = measure_read_bw(sell, stream)
+        gather_gps = measure_gather(sell, stream, max(A.ncols, 1))
+        fma_tf = measure_fp64_fma(sell, stream)
 
-        # ---- measuring kernels: read bandwidth b (Listing "reduction" analogue), FP64 FMA peak
-        b_read = measure_read_bw(sell, stream) if rank == 0 else None
-        fma_tf = measure_fp64_fma(sell, stream) if rank == 0 else None
+        # ---- autotuner: stage 1 = the (C, sigma) sweep, stage 2 = launch shapes
+        if args.C is not None or args.sigma is not None or args.no_sweep:
+            Cs, sigmas = (args.C or 32,), (args.sigma or 1,)
+        else:
+            Cs, sigmas = sorted({c for c, _ in grid}), sorted({s for _, s in grid})
+        tr = autotune.tune(csr_d, store_type=sell.SELL_F64, Cs=Cs, sigmas=sigmas, blocks=(128, 256, 512),
+                           unrolls=(1, 2, 4, 8), keep=2, stream=stream, use_cache=False, cache=None)
+        best = tr.best
+        C, sigma = best.C, best.sigma
+        t0 = time.perf_counter()
+        h = autotune.build_tuned(csr_d, best, stream=stream)
+        build_ms = (time.perf_counter() - t0) * 1e3
+        inf = h.info
+        sweep = [{"C": f["C"], "sigma": f["sigma"], "beta": round(f["beta"], 4), "us": round(f["us"], 2),
+                  "gflops": round(2.0 * A.nnz / f["us"] / 1e3, 1), "build_ms": round(f["build_ms"], 2)}
+                 for f in sorted(tr.formats, key=lambda f: (f["C"], f["sigma"]))]
 
         # ---- the timed region: K steps of one SpMV each
         clk = ClockSampler(local)
@@ -355,12 +432,14 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
         wall0 = time.time()
+        torch.cuda.nvtx.range_push("timed_region")
         t_start.record(stream)
         for i in range(args.steps):
             ev_a[i].record(stream)
             sell.sell_spmv(h, xd, yd, stream=stream)
             ev_b[i].record(stream)
         t_end.record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
@@ -408,6 +487,7 @@ def run_ours(args):
 
             # ---- reduced-precision storage: binary32 / bfloat16 values, binary32 accumulation
             mixed = {}
+            sell.sell_spmv(h, xd, yd, stream=stream)
             y64 = yd.clone()
             x32 = xd.float()
             for name, st in (("f32", sell.SELL_F32), ("bf16", sell.SELL_BF16)):
@@ -415,40 +495,51 @@ def run_ours(args):
                 y32 = torch.empty(A.nrows, dtype=torch.float32, device="cuda")
                 row = {}
                 for tag, fl in (("plain", 0), ("dot2", sell.SELL_SPMV_COMPENSATED)):
+                    blk, unr, _ = tune_launch(sell, hm, x32, y32, stream, flags=fl)
                     dt = time_spmv(sell, hm, x32, y32, stream, reps=100, flags=fl)
                     torch.cuda.synchronize()
                     err = (y32.double() - y64).abs()
                     row[tag] = {"gflops": round(flops / dt / 1e9, 1), "us": round(dt * 1e6, 2),
-                                "speedup_vs_f64": round(step_s / dt, 3),
+                                "speedup_vs_f64": round(kern_s / dt, 3), "block": blk, "unroll": unr,
                                 "max_abs_err_vs_f64": float(err.max()),
                                 "rel_err_vs_f64": float(err.norm() / y64.norm())}
                 mixed[name] = row
                 hm.free()
             extras["mixed"] = mixed
+        del csr_d
+        torch.cuda.empty_cache()
+        if not args.no_extras and args.workload == "lognormal" and rank == 0:
+            extras["stencil27"] = stencil_section(sell, model, stream, peak, fma_tf)
 
     # ---- roofline of the dominant kernel (the SpMV)
-    peak, peak_src = load_peaks()
     alg = model.algorithmic_bytes(A.nrows, A.ncols, A.nnz, inf.nchunks, C, 8, 8, inf.has_perm)
     achieved = alg / kern_s / 1e9
-    wl_key = f"{args.workload}:C{C}:s{sigma}:N{A.nrows}"
+    wl_key = f"{args.workload}:N{A.nrows}"
     traffic, _ = lookup_traffic(wl_key)
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": traffic,
             "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
-            "kernel": "k_spmmv<double,1,U,Plain<double>>", "kernel_avg_us": round(kern_s * 1e6, 3),
-            "algorithmic_bytes_per_launch": alg}
-    pm_bytes = model.paper_model_bytes(A.nnz, inf.beta, A.nrows, A.ncols)
+            "kernel": f"k_spmmv<double,1,{best.unroll},Plain<double>> block {best.block}",
+            "kernel_avg_us": round(kern_s * 1e6, 3), "algorithmic_bytes_per_launch": alg}
     nnzr = A.nnz / A.nrows
+    bal = model.balance_sell(1.0 / nnzr, inf.beta, nnzr)
+    extras["gather_bound"] = {
+        "note": "every nonzero gathers one x element from L2 (x is L2-resident): random columns are bound "
+                "by the L2 scattered-sector rate measured by sell_bench_gather",
+        "gathers_per_launch": A.nnz, "achieved_ggps": round(A.nnz / kern_s / 1e9, 1),
+        "peak_ggps_measured": round(gather_gps, 1), "frac": round(A.nnz / kern_s / 1e9 / gather_gps, 4),
+        "bound_us": round(A.nnz / gather_gps / 1e3, 2)}
     extras["paper_model"] = {
         "beta": inf.beta, "nnzr": round(nnzr, 3), "zeta": round(inf.zeta, 3),
-        "balance_bytes_per_flop": round(model.balance_sell(1.0 / nnzr, inf.beta, nnzr), 4),
-        "bound_gflops_measured_b": round(model.roofline(b_read or peak, model.balance_sell(1.0 / nnzr, inf.beta, nnzr)), 1),
-        "frac_of_model_bound": round(value / n_gpus / model.roofline(b_read or peak, model.balance_sell(1.0 / nnzr, inf.beta, nnzr)), 4),
-        "model_bytes_per_launch": int(pm_bytes)}
-    extras["b_read_gbs"] = round(b_read, 1) if b_read else None
-    extras["fp64_fma_peak_tflops"] = round(fma_tf, 3) if fma_tf else None
-    extras["fp64_pipe_frac"] = round(flops / kern_s / 1e12 / fma_tf, 4) if fma_tf else None
+        "balance_bytes_per_flop": round(bal, 4),
+        "bound_gflops_b_read": round(model.roofline(b_read, bal), 1),
+        "frac_of_model_bound": round(value / n_gpus / model.roofline(b_read, bal), 4),
+        "model_bytes_per_launch": int(model.paper_model_bytes(A.nnz, inf.beta, A.nrows, A.ncols))}
+    extras["b_read_gbs"] = round(b_read, 1)
+    extras["fp64_fma_peak_tflops"] = round(fma_tf, 3)
+    extras["fp64_pipe_frac"] = round(flops / kern_s / 1e12 / fma_tf, 4)
     extras["build_ms"] = round(build_ms, 2)
+    extras["tuned"] = {"C": C, "sigma": sigma, "block": best.block, "unroll": best.unroll}
     extras["sweep"] = sweep
     extras["device"] = dev_name
 

@@ -265,6 +265,17 @@ SELL_API sell_status sell_batch_free(sell_batch_plan plan);
 SELL_API sell_status sell_bench_read(const void *buf, size_t bytes, double *sink, int32_t grid,
                             void *stream);
 
+/* Random-gather rate kernel: grid x 256 threads each load iters x 8
+ * 8-byte words x[h % n] at pseudo-random positions h (a linear congruential
+ * sequence) and write one value each to `sink` (device, grid*256 doubles).
+ * With x (n <= 2^32 - 1 words, 8-byte aligned) small enough to stay in L2,
+ * gathers per second measure how fast L2 serves scattered 32-byte sectors:
+ * the co-bound of an SpMV with random column indices, where every nonzero
+ * gathers one x element (the access that alpha models in Sec. 4, whose
+ * model assumes infinitely fast caches).  Errors: SELL_EINVAL, SELL_ECUDA. */
+SELL_API sell_status sell_bench_gather(const void *x, int64_t n, double *sink, int32_t grid, int32_t iters,
+                                       void *stream);
+
 /* Binary64 fused multiply-add throughput kernel: every thread of
  * grid x 256 threads runs `iters` x 64 dependent-chain FMAs on 8 independent
  * chains; `sink` (device, grid*256 doubles) receives the results.  Used to

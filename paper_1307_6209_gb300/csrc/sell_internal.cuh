@@ -119,6 +119,7 @@ sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s
 sell_status batch_run(const sell_batch *b, int32_t grid, cudaStream_t s);
 sell_status bench_read(const void *buf, size_t bytes, double *sink, int32_t grid, cudaStream_t s);
 sell_status bench_fma64(double *sink, int32_t grid, int32_t iters, cudaStream_t s);
+sell_status bench_gather(const void *x, int64_t n, double *sink, int32_t grid, int32_t iters, cudaStream_t s);
 
 // --------------------------------------------------------- device helpers
 // Streaming loads for data touched once per product (val/col): do not allocate

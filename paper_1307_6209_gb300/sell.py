@@ -87,6 +87,7 @@ SIGNATURES = {
     "sell_batch_free": (ctypes.c_int, [_P]),
     "sell_bench_read": (ctypes.c_int, [_P, ctypes.c_size_t, _P, ctypes.c_int32, _P]),
     "sell_bench_fma64": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P]),
+    "sell_bench_gather": (ctypes.c_int, [_P, ctypes.c_int64, _P, ctypes.c_int32, ctypes.c_int32, _P]),
 }
 
 _lib = None
@@ -326,6 +327,10 @@ def sell_batch_free(plan: BatchPlan):
 # ------------------------------------------------------------------ measuring
 def sell_bench_read(buf, nbytes: int, sink, grid: int = 0, stream=None):
     _check(load().sell_bench_read(_ptr(buf), int(nbytes), _ptr(sink), int(grid), _stream_ptr(stream)))
+
+
+def sell_bench_gather(x, n: int, sink, grid: int, iters: int, stream=None):
+    _check(load().sell_bench_gather(_ptr(x), int(n), _ptr(sink), int(grid), int(iters), _stream_ptr(stream)))
 
 
 def sell_bench_fma64(sink, grid: int, iters: int, stream=None):

@@ -210,3 +210,43 @@ def vector(n: int, seed: int = 0, lo: float = -1.0, hi: float = 1.0) -> np.ndarr
 def block(n: int, k: int, seed: int = 0) -> np.ndarray:
     """Row-major n x k block of right-hand sides, U[-1, 1]."""
     return np.random.default_rng(seed).uniform(-1.0, 1.0, (n, k))
+
+
+def stencil27_device(n: int, perturb: float = 0.1, seed: int = 0, device: str = "cuda") -> CSR:
+    """The 27-point stencil of ``stencil27`` generated on the GPU with torch
+    (same structure and base values; the perturbation factors come from
+    torch's seeded device generator, so they differ from the numpy version).
+    rpt/col/val are CUDA tensors."""
+    import torch
+
+    N = n ** 3
+    idx = torch.arange(N, device=device, dtype=torch.int64)
+    gx, gy, gz = idx % n, (idx // n) % n, idx // (n * n)
+
+    def span(g):
+        return 3 - (g == 0).to(torch.int64) - (g == n - 1).to(torch.int64)
+
+    rl = span(gx) * span(gy) * span(gz) if n > 1 else torch.ones(N, dtype=torch.int64, device=device)
+    rpt = torch.zeros(N + 1, dtype=torch.int64, device=device)
+    torch.cumsum(rl, 0, out=rpt[1:])
+    nnz = int(rpt[-1])
+    col = torch.empty(nnz, dtype=torch.int32, device=device)
+    val = torch.empty(nnz, dtype=torch.float64, device=device)
+    cnt = torch.zeros(N, dtype=torch.int64, device=device)
+    start = rpt[:-1]
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                ok = ((gx + dx >= 0) & (gx + dx < n) & (gy + dy >= 0) & (gy + dy < n)
+                      & (gz + dz >= 0) & (gz + dz < n))
+                rows = torch.nonzero(ok, as_tuple=True)[0]
+                pos = start[rows] + cnt[rows]
+                col[pos] = (rows + dz * n * n + dy * n + dx).to(torch.int32)
+                val[pos] = 26.0 if (dx, dy, dz) == (0, 0, 0) else -1.0
+                cnt += ok.to(torch.int64)
+                del ok, rows, pos
+    if perturb:
+        g = torch.Generator(device=device)
+        g.manual_seed(seed)
+        val *= 1.0 + perturb * (2.0 * torch.rand(nnz, generator=g, dtype=torch.float64, device=device) - 1.0)
+    return CSR(N, N, rpt, col, val)
