@@ -371,6 +371,166 @@ def stencil_section(sell, model, stream, peak, fma_tf, n=200):
     return out
 
 
+def _time_graph(g, stream, reps):
+    import torch
+    g.replay()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        g.replay()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) * 1e-3 / reps
+
+
+def batched_section(sell, autotune, stream, nmat=512, ks=(1, 4, 8), seed=0):
+    """512 matrices, rows U[1k, 200k], half banded (bandwidth 64, 7-30 per
+    row), half lognormal; FP32 storage; k right-hand sides; C and sigma tuned
+    per class.  One persistent launch (CUDA graph) against per-matrix launches
+    and against the same batch in FP64."""
+    import torch
+    from paper_1307_6209_gb300 import synth
+    gen = {"banded": synth.banded_device, "lognormal": synth.lognormal_device}
+    rng = np.random.default_rng(seed)
+    sizes = rng.integers(1000, 200001, nmat)
+    choice = {}
+    for cls in ("banded", "lognormal"):
+        A = gen[cls](100_000, seed=999)
+        tr = autotune.tune(A, store_type=sell.SELL_F32, Cs=(32, 64), sigmas=(1, 256, 4096, 1 << 30),
+                           blocks=(256,), unrolls=(2, 4), keep=1, stream=stream, use_cache=False, cache=None)
+        choice[cls] = {"C": tr.best.C, "sigma": tr.best.sigma}
+        del A
+    h32, h64, nnz = [], [], 0
+    t0 = time.perf_counter()
+    for i, n in enumerate(sizes):
+        cls = "banded" if i % 2 == 0 else "lognormal"
+        A = gen[cls](int(n), seed=i)
+        ch = choice[cls]
+        h32.append(sell.sell_build(A, C=ch["C"], sigma=ch["sigma"], store_type=sell.SELL_F32, stream=stream))
+        h64.append(sell.sell_build(A, C=ch["C"], sigma=ch["sigma"], store_type=sell.SELL_F64, stream=stream))
+        nnz += A.nnz
+        del A
+    build_s = time.perf_counter() - t0
+    out = {"workload": f"{nmat} matrices, rows U[1000, 200000], half banded (bw 64, 7-30/row), half lognormal",
+           "nnz_total": nnz, "rows_total": int(sizes.sum()), "tuned": choice,
+           "build_s_both_precisions": round(build_s, 2)}
+    for k in ks:
+        row = {}
+        for tag, hs, dt in (("f32", h32, torch.float32), ("f64", h64, torch.float64)):
+            items = []
+            for h in hs:
+                shp_x = (h.info.ncols,) if k == 1 else (h.info.ncols, k)
+                shp_y = (h.info.nrows,) if k == 1 else (h.info.nrows, k)
+                items.append((h, torch.rand(shp_x, dtype=dt, device="cuda"),
+                              torch.empty(shp_y, dtype=dt, device="cuda"), 0))
+            plan = sell.sell_batch_create(items, stream=stream)
+            plan.run(stream=stream)
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                plan.run(stream=stream)
+            t_batch = _time_graph(g, stream, 20)
+
+            def per_matrix():
+                for h, X, Y, _ in items:
+                    if k == 1:
+                        sell.sell_spmv(h, X, Y, stream=stream)
+                    else:
+                        sell.sell_spmmv(h, X, Y, stream=stream)
+            per_matrix()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(3):
+                per_matrix()
+            b.record(stream)
+            b.synchronize()
+            t_eager = a.elapsed_time(b) * 1e-3 / 3
+            g2 = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g2, stream=stream):
+                per_matrix()
+            t_pm_graph = _time_graph(g2, stream, 5)
+            row[tag] = {"batch_ms": round(t_batch * 1e3, 3), "gflops": round(2.0 * nnz * k / t_batch / 1e9, 1),
+                        "per_matrix_eager_ms": round(t_eager * 1e3, 3),
+                        "per_matrix_graph_ms": round(t_pm_graph * 1e3, 3),
+                        "speedup_vs_per_matrix_eager": round(t_eager / t_batch, 2),
+                        "speedup_vs_per_matrix_graph": round(t_pm_graph / t_batch, 2)}
+            plan.free()
+            del g, g2, items
+        row["f32_speedup_vs_f64"] = round(row["f64"]["batch_ms"] / row["f32"]["batch_ms"], 3)
+        out[f"k{k}"] = row
+    for h in h32 + h64:
+        h.free()
+    torch.cuda.empty_cache()
+    return out
+
+
+def serving_section(sell, stream, nmat=64, seed=0, duration_s=1.5):
+    """64 resident matrices, rows log-uniform in [10k, 4M], lognormal row
+    lengths, half FP64 and half FP32; requests of 1-8 right-hand sides from
+    pinned host memory; Poisson arrivals at fractions of the saturated rate."""
+    import torch
+    from paper_1307_6209_gb300 import serving, synth
+    rng = np.random.default_rng(seed)
+    rows = np.exp(rng.uniform(np.log(10_000), np.log(4_000_000), nmat)).astype(np.int64)
+    mats = []
+    for i, n in enumerate(rows):
+        A = synth.lognormal_device(int(n), seed=1000 + i)
+        st = sell.SELL_F64 if i % 2 == 0 else sell.SELL_F32
+        mats.append(sell.sell_build(A, C=32, sigma=int(n), store_type=st, stream=stream))
+        del A
+    resident = sum(h.info.device_bytes for h in mats)
+    budget = resident + (8 << 30)
+    # one pinned input block per (matrix, k): inputs are read-only
+    pool = {}
+
+    def make(g):
+        mid = int(g.integers(0, nmat))
+        k = int(g.integers(1, 9))
+        key = (mid, k)
+        if key not in pool:
+            inf = mats[mid].info
+            dt = torch.float64 if inf.store_type == sell.SELL_F64 else torch.float32
+            shp = (inf.ncols,) if k == 1 else (inf.ncols, k)
+            pool[key] = (torch.rand(shp, dtype=dt) * 2 - 1).pin_memory()
+        return mid, pool[key]
+
+    # saturated throughput: a burst of requests submitted at once
+    srv = serving.Server(mats, budget, max_batch=64, streams=3).start()
+    g = np.random.default_rng(1)
+    for _ in range(16):
+        make(g)
+    t0 = time.perf_counter()
+    burst = [srv.submit(*make(g)) for _ in range(400)]
+    for r in burst:
+        r.done.wait(120)
+    sat = len(burst) / (time.perf_counter() - t0)
+    srv.stop()
+    out = {"workload": f"{nmat} resident matrices, rows log-uniform [10k, 4M], lognormal rows, half FP64 / "
+                       f"half FP32, requests k ~ U{{1..8}}, inputs from pinned host memory",
+           "resident_gb": round(resident / 1e9, 2), "budget_gb": round(budget / 1e9, 2),
+           "nnz_total": int(sum(h.info.nnz for h in mats)),
+           "saturated_req_per_s": round(sat, 1), "burst": srv.stats()}
+    for frac in (0.5, 0.8):
+        srv = serving.Server(mats, budget, max_batch=64, streams=3).start()
+        reqs = serving.poisson_load(srv, rate_hz=frac * sat, duration_s=duration_s, make_request=make, seed=7)
+        for r in reqs:
+            r.done.wait(120)
+        t_end = max(r.t_done for r in reqs)
+        st = srv.stats()
+        srv.stop()
+        gfl = sum(2.0 * mats[r.mid].info.nnz * r.k for r in reqs)
+        st["throughput_req_per_s"] = round(len(reqs) / (t_end - min(r.t_arrive for r in reqs)), 1)
+        st["gflops"] = round(gfl / (t_end - min(r.t_arrive for r in reqs)) / 1e9, 1)
+        st["offered_req_per_s"] = round(frac * sat, 1)
+        out[f"load_{frac}"] = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in st.items()}
+    for h in mats:
+        h.free()
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_1307_6209_gb300 import autotune
@@ -510,6 +670,8 @@ def run_ours(args):
         torch.cuda.empty_cache()
         if not args.no_extras and args.workload == "lognormal" and rank == 0:
             extras["stencil27"] = stencil_section(sell, model, stream, peak, fma_tf)
+            extras["batched"] = batched_section(sell, autotune, stream)
+            extras["serving"] = serving_section(sell, stream)
 
     # ---- roofline of the dominant kernel (the SpMV)
     alg = model.algorithmic_bytes(A.nrows, A.ncols, A.nnz, inf.nchunks, C, 8, 8, inf.has_perm)

@@ -240,9 +240,11 @@ typedef struct sell_batch *sell_batch_plan;
  * use matrices of different sizes and storage types; a matrix with more than
  * 8 right-hand sides is split into blocks of 8.  Each result is bit-identical
  * to the same product run alone by sell_spmmv.  The plan owns its device
- * table; the items' buffers are referenced, not copied.  Several products in
- * one plan must not write overlapping Y.  Errors: SELL_EINVAL, SELL_ENOMEM,
- * SELL_ECUDA. */
+ * table and the long-row scratch of its products (so plans never share
+ * scratch with each other or with sell_spmmv); the items' buffers are
+ * referenced, not copied.  Several products in one plan must not write
+ * overlapping Y.  Synchronises `stream` once (after uploading the tables).
+ * Errors: SELL_EINVAL, SELL_ENOMEM, SELL_ECUDA. */
 SELL_API sell_status sell_batch_create(const sell_batch_item *items, int32_t n, void *stream,
                               sell_batch_plan *out);
 
@@ -251,7 +253,9 @@ SELL_API sell_status sell_batch_create(const sell_batch_item *items, int32_t n, 
  * Errors: SELL_EINVAL, SELL_ECUDA. */
 SELL_API sell_status sell_batch_run(sell_batch_plan plan, int32_t grid, void *stream);
 
-/* Release a plan (NULL accepted). */
+/* Release a plan (NULL accepted).  The memory is returned stream-ordered on
+ * the stream of the plan's latest sell_batch_run (no host wait); a plan run
+ * on several streams must have finished its runs on the other streams. */
 SELL_API sell_status sell_batch_free(sell_batch_plan plan);
 
 /* ------------------------------------------------------------ measuring */

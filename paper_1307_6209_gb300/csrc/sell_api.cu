@@ -262,12 +262,13 @@ sell_status sell_batch_run(sell_batch_plan plan, int32_t grid, void *stream) {
 
 sell_status sell_batch_free(sell_batch_plan plan) {
     if (!plan) return SELL_OK;
-    (void)cudaDeviceSynchronize();
-    plan->al.put(plan->items, nullptr);
-    plan->al.put(plan->units, nullptr);
-    plan->al.put(plan->counter, nullptr);
-    for (void *p : plan->scratch) plan->al.put(p, nullptr);
-    (void)cudaDeviceSynchronize();
+    // stream-ordered release after the latest run (no host wait), so a
+    // scheduler can retire finished plans while other batches still run
+    cudaStream_t s = plan->ran ? plan->last_stream : nullptr;
+    plan->al.put(plan->items, s);
+    plan->al.put(plan->units, s);
+    plan->al.put(plan->counter, s);
+    for (void *p : plan->scratch) plan->al.put(p, s);
     delete plan;
     return SELL_OK;
 }

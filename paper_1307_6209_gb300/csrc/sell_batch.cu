@@ -207,7 +207,9 @@ sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s
     return SELL_OK;
 }
 
-sell_status batch_run(const sell_batch *b, int32_t grid, cudaStream_t s) {
+sell_status batch_run(sell_batch *b, int32_t grid, cudaStream_t s) {
+    b->last_stream = s;
+    b->ran = true;
     if (b->nwork == 0) return SELL_OK;
     int g = grid > 0 ? grid : b->grid_default;
     SELL_CUDA_TRY(cudaMemsetAsync(b->counter, 0, sizeof(unsigned int), s));

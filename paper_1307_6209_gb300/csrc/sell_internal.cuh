@@ -103,6 +103,8 @@ struct sell_batch {
     int64_t nwork = 0;
     int32_t nprod = 0;
     int32_t grid_default = 0;
+    cudaStream_t last_stream = nullptr;  // stream of the latest sell_batch_run
+    bool ran = false;
 };
 
 namespace sell {
@@ -116,7 +118,7 @@ sell_status launch_block_with_scratch(const sell_matrix *h, const void *X, int64
                                       cudaStream_t s);
 sell_status build_format(const sell_csr *A, const sell_opts *o, cudaStream_t s, sell_matrix *h);
 sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s, sell_batch *b);
-sell_status batch_run(const sell_batch *b, int32_t grid, cudaStream_t s);
+sell_status batch_run(sell_batch *b, int32_t grid, cudaStream_t s);
 sell_status bench_read(const void *buf, size_t bytes, double *sink, int32_t grid, cudaStream_t s);
 sell_status bench_fma64(double *sink, int32_t grid, int32_t iters, cudaStream_t s);
 sell_status bench_gather(const void *x, int64_t n, double *sink, int32_t grid, int32_t iters, cudaStream_t s);

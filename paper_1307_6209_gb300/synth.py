@@ -250,3 +250,65 @@ def stencil27_device(n: int, perturb: float = 0.1, seed: int = 0, device: str = 
         g.manual_seed(seed)
         val *= 1.0 + perturb * (2.0 * torch.rand(nnz, generator=g, dtype=torch.float64, device=device) - 1.0)
     return CSR(N, N, rpt, col, val)
+
+
+def _distinct_sorted_columns_device(rl, lo, hi, gen):
+    """Device version of _distinct_sorted_columns (torch): rl[i] distinct
+    integers uniform in [lo[i], hi[i]) per row, sorted, rows concatenated."""
+    import torch
+    dev = rl.device
+    N = rl.shape[0]
+    rows = torch.repeat_interleave(torch.arange(N, device=dev, dtype=torch.int64), rl)
+    span = (hi - lo)[rows]
+    base = lo[rows]
+    width = int(max(1, int((hi - lo).max()))) if N else 1
+
+    def draw(m, sp):
+        r = torch.randint(0, 2 ** 62, (m,), generator=gen, device=dev, dtype=torch.int64)
+        return r % sp
+
+    off = draw(rows.shape[0], span)
+    while True:
+        key = rows * width + off
+        key, order = torch.sort(key)
+        off = off[order]
+        dup = torch.nonzero(key[1:] == key[:-1], as_tuple=True)[0] + 1
+        if dup.numel() == 0:
+            return (base + off)
+        off[dup] = draw(dup.numel(), span[dup])
+
+
+def lognormal_device(N: int, mean: float = 16.0, sigma_ln: float = 1.2, cap: int = 2000, seed: int = 0,
+                     device: str = "cuda") -> CSR:
+    """The ``lognormal`` recipe generated with torch on the device (own seeded
+    stream, so the values differ from the numpy version)."""
+    import math
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    mu = math.log(mean) - 0.5 * sigma_ln * sigma_ln
+    z = torch.randn(N, generator=g, device=device, dtype=torch.float64)
+    rl = torch.clamp(torch.round(torch.exp(mu + sigma_ln * z)), 1, min(cap, N)).to(torch.int64)
+    col = _distinct_sorted_columns_device(rl, torch.zeros(N, dtype=torch.int64, device=device),
+                                          torch.full((N,), N, dtype=torch.int64, device=device), g)
+    val = torch.randn(col.shape[0], generator=g, device=device, dtype=torch.float64)
+    rpt = torch.zeros(N + 1, dtype=torch.int64, device=device)
+    torch.cumsum(rl, 0, out=rpt[1:])
+    return CSR(N, N, rpt, col.to(torch.int32), val)
+
+
+def banded_device(N: int, bandwidth: int = 64, lo: int = 7, hi: int = 30, seed: int = 0,
+                  device: str = "cuda") -> CSR:
+    """The ``banded`` recipe generated with torch on the device."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    i = torch.arange(N, device=device, dtype=torch.int64)
+    a = torch.clamp(i - bandwidth, min=0)
+    b = torch.clamp(i + bandwidth + 1, max=N)
+    rl = torch.minimum(torch.randint(lo, hi + 1, (N,), generator=g, device=device, dtype=torch.int64), b - a)
+    col = _distinct_sorted_columns_device(rl, a, b, g)
+    val = torch.randn(col.shape[0], generator=g, device=device, dtype=torch.float64)
+    rpt = torch.zeros(N + 1, dtype=torch.int64, device=device)
+    torch.cumsum(rl, 0, out=rpt[1:])
+    return CSR(N, N, rpt, col.to(torch.int32), val)
