@@ -234,23 +234,25 @@ typedef struct {
 
 typedef struct sell_batch *sell_batch_plan;
 
-/* Prepare a batch of n products for one persistent launch: a device table of
- * work items (one per tile of 256 sorted rows of one product) that the
- * persistent kernel's blocks claim with an atomic counter.  The products may
- * use matrices of different sizes and storage types; a matrix with more than
- * 8 right-hand sides is split into blocks of 8.  Each result is bit-identical
- * to the same product run alone by sell_spmmv.  The plan owns its device
- * table and the long-row scratch of its products (so plans never share
- * scratch with each other or with sell_spmmv); the items' buffers are
- * referenced, not copied.  Several products in one plan must not write
- * overlapping Y.  Synchronises `stream` once (after uploading the tables).
- * Errors: SELL_EINVAL, SELL_ENOMEM, SELL_ECUDA. */
+/* Prepare a batch of n products to run in a few launches (one per kernel
+ * variant present -- value type, block of 1/2/4/8 right-hand sides, plain or
+ * compensated accumulation -- and per 192 products).  Work units are tiles of
+ * 256 sorted rows of one product, or 256 threads of its long-row segment
+ * work; every launch has one block per unit, long-row work first and the
+ * biggest products first.  The products may use matrices of different sizes
+ * and storage types; a matrix with more than 8 right-hand sides is split
+ * into blocks of 8.  Each result is bit-identical to the same product run
+ * alone by sell_spmmv.  The plan owns its device tables and the long-row
+ * scratch of its products (so plans never share scratch with each other or
+ * with sell_spmmv); the items' buffers are referenced, not copied.  Several
+ * products in one plan must not write overlapping Y.  Synchronises `stream`
+ * (after uploading the tables).  Errors: SELL_EINVAL, SELL_ENOMEM,
+ * SELL_ECUDA. */
 SELL_API sell_status sell_batch_create(const sell_batch_item *items, int32_t n, void *stream,
                               sell_batch_plan *out);
 
-/* Launch a plan on `stream` (capturable in a CUDA graph: one memset and one
- * kernel).  grid = 0 picks one block per SM times the occupancy.
- * Errors: SELL_EINVAL, SELL_ECUDA. */
+/* Launch a plan on `stream` (kernel launches only: capturable in a CUDA
+ * graph).  grid must be 0 (reserved).  Errors: SELL_EINVAL, SELL_ECUDA. */
 SELL_API sell_status sell_batch_run(sell_batch_plan plan, int32_t grid, void *stream);
 
 /* Release a plan (NULL accepted).  The memory is returned stream-ordered on

@@ -245,7 +245,7 @@ sell_status sell_batch_create(const sell_batch_item *items, int32_t n, void *str
     if (st != SELL_OK) {
         std::string msg = g_last_error;
         (void)cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
-        for (void *p : b->scratch) b->al.put(p, nullptr);
+        batch_release(b, nullptr);
         (void)cudaDeviceSynchronize();
         delete b;
         g_last_error = msg;
@@ -265,10 +265,7 @@ sell_status sell_batch_free(sell_batch_plan plan) {
     // stream-ordered release after the latest run (no host wait), so a
     // scheduler can retire finished plans while other batches still run
     cudaStream_t s = plan->ran ? plan->last_stream : nullptr;
-    plan->al.put(plan->items, s);
-    plan->al.put(plan->units, s);
-    plan->al.put(plan->counter, s);
-    for (void *p : plan->scratch) plan->al.put(p, s);
+    batch_release(plan, s);
     delete plan;
     return SELL_OK;
 }

@@ -1,16 +1,24 @@
-// sell_batch.cu -- many SELL-C-sigma products in one persistent launch.
+// sell_batch.cu -- many SELL-C-sigma products in persistent launches.
 //
-// A plan holds a device table of products and one of work units; a unit is
-// (product, first sorted row, first right-hand-side column), i.e. a tile of
-// kTileRows sorted rows of one product for up to 8 right-hand sides.  The
-// persistent kernel runs one or a few blocks per SM; each block claims units
-// with an atomic counter until the table is exhausted, so small and large
-// matrices share the machine without per-matrix launches or tail gaps.
+// A plan splits every product into column blocks of 8, 4, 2 or 1 right-hand
+// sides and groups the blocks by kernel variant (value type, block width,
+// plain or compensated accumulation).  Each variant present gets one launch
+// (per 192 products): its products travel in the kernel's parameter space and
+// a device table lists the work units -- a unit is kTileRows sorted rows of
+// one product (its short rows), or kTileRows threads of the product's
+// long-row segment units.  One block per unit, long-row units first and
+// biggest products first; the hardware block scheduler balances the uneven
+// products.  (A grid-stride "persistent" form of this kernel was measured:
+// its loop-carried state raised the register count from 40 to 64, cut the
+// resident blocks per SM from 6 to 4 and made the batch slower.)
 //
-// Every row is computed by the same per-thread loop as sell_spmmv (CRS order,
-// one FMA or one Dot2 step per stored nonzero), so a product's result is
-// bit-identical whether it runs alone or inside any batch.
+// Every row is computed by the same per-row arithmetic as sell_spmmv
+// (sell_rowdot.cuh), so a product's result is bit-identical whether it runs
+// alone or inside any batch.
 #include <algorithm>
+#include <map>
+#include <new>
+#include <tuple>
 #include <vector>
 
 #include "sell_rowdot.cuh"
@@ -44,61 +52,60 @@ struct Unit {
     int64_t idx;
 };
 
+// The products of one launch travel in the kernel's parameter space (read
+// through the constant cache when a unit needs a field), which keeps the
+// register footprint at that of the single-product kernel.
+constexpr int kLaunchProds = 192;  // 192 * 144 B fits the 32 KB parameter limit
+
+struct LaunchParams {
+    Prod prods[kLaunchProds];
+    const Unit *units;
+    int64_t nwork;
+};
+
+// One block per work unit, long-row units first in the grid so that they
+// start early (the same shape as the single-product kernel).
 template <class VT, int K, class Acc>
-__device__ __noinline__ void do_unit(const Prod &P, const Unit &u, uint64_t pol) {
+__global__ void __launch_bounds__(kTileRows)
+k_batch(const __grid_constant__ LaunchParams lp) {
     using XT = typename XType<VT>::T;
-    constexpr int U = K >= 8 ? 2 : (K >= 4 ? 4 : 8);
-    const VT *val = static_cast<const VT *>(P.val);
-    const XT *X = static_cast<const XT *>(P.X);
-    XT *Y = static_cast<XT *>(P.Y);
+    constexpr int U = K >= 4 ? 2 : 4;
+    const uint64_t pol = l2_evict_first_policy();
+    const int64_t w = blockIdx.x;
+    if (w >= lp.nwork) return;
+    const Unit u = lp.units[w];
+    const Prod &P = lp.prods[u.prod];
     if (u.kind == 1) {
         const int64_t v = u.idx + threadIdx.x;
         if (v < P.long_threads)
-            long_unit<VT, XT, K, U, Acc>(val, P.col, P.cs, P.srl, P.perm, P.lchunk, P.lunit,
-                                         static_cast<Acc *>(P.part), P.cnt, X, P.ldx, Y, P.ldy, P.N, P.C, v,
-                                         P.acc, P.vec != 0, pol);
-    } else {
-        const int64_t r = u.idx + threadIdx.x;
-        if (r < P.N)
-            short_row<VT, XT, K, U, Acc>(val, P.col, P.cs, P.srl, P.perm, X, P.ldx, Y, P.ldy, P.C, r, P.acc,
-                                         P.vec != 0, pol);
+            long_unit<VT, XT, K, U, Acc>(static_cast<const VT *>(P.val), P.col, P.cs, P.srl, P.perm, P.lchunk,
+                                         P.lunit, static_cast<Acc *>(P.part), P.cnt, static_cast<const XT *>(P.X),
+                                         P.ldx, static_cast<XT *>(P.Y), P.ldy, P.N, P.C, v, P.acc, P.vec != 0, pol);
+        return;
     }
+    const int64_t r = u.idx + threadIdx.x;
+    if (r < P.N)
+        short_row<VT, XT, K, U, Acc>(static_cast<const VT *>(P.val), P.col, P.cs, P.srl, P.perm,
+                                     static_cast<const XT *>(P.X), P.ldx, static_cast<XT *>(P.Y), P.ldy, P.C, r, P.acc,
+                                     P.vec != 0, pol);
 }
+
+using KernelFn = void (*)(const LaunchParams);
 
 template <class VT, class Acc>
-__device__ __forceinline__ void dispatch_k(const Prod &P, const Unit &u, uint64_t pol) {
-    switch (P.kb) {
-        case 1: do_unit<VT, 1, Acc>(P, u, pol); break;
-        case 2: do_unit<VT, 2, Acc>(P, u, pol); break;
-        case 4: do_unit<VT, 4, Acc>(P, u, pol); break;
-        default: do_unit<VT, 8, Acc>(P, u, pol); break;
+KernelFn kernel_for_k(int kb) {
+    switch (kb) {
+        case 1: return k_batch<VT, 1, Acc>;
+        case 2: return k_batch<VT, 2, Acc>;
+        case 4: return k_batch<VT, 4, Acc>;
+        default: return k_batch<VT, 8, Acc>;
     }
 }
 
-__global__ void __launch_bounds__(kTileRows)
-k_batch(const Prod *__restrict__ prods, const Unit *__restrict__ units, int64_t nwork,
-        unsigned int *counter) {
-    __shared__ int64_t s_unit;
-    const uint64_t pol = l2_evict_first_policy();
-    for (;;) {
-        if (threadIdx.x == 0) s_unit = (int64_t)atomicAdd(counter, 1u);
-        __syncthreads();
-        const int64_t w = s_unit;
-        __syncthreads();
-        if (w >= nwork) break;
-        const Unit u = units[w];
-        const Prod P = prods[u.prod];
-        if (P.type == SELL_F64) {
-            dispatch_k<double, Plain<double>>(P, u, pol);
-        } else if (P.type == SELL_F32) {
-            if (P.comp) dispatch_k<float, Dot2>(P, u, pol);
-            else dispatch_k<float, Plain<float>>(P, u, pol);
-        } else {
-            if (P.comp) dispatch_k<__nv_bfloat16, Dot2>(P, u, pol);
-            else dispatch_k<__nv_bfloat16, Plain<float>>(P, u, pol);
-        }
-        __syncthreads();
-    }
+KernelFn kernel_for(int type, int comp, int kb) {
+    if (type == SELL_F64) return kernel_for_k<double, Plain<double>>(kb);
+    if (type == SELL_F32) return comp ? kernel_for_k<float, Dot2>(kb) : kernel_for_k<float, Plain<float>>(kb);
+    return comp ? kernel_for_k<__nv_bfloat16, Dot2>(kb) : kernel_for_k<__nv_bfloat16, Plain<float>>(kb);
 }
 
 }  // namespace
@@ -106,7 +113,6 @@ k_batch(const Prod *__restrict__ prods, const Unit *__restrict__ units, int64_t 
 sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s, sell_batch *b) {
     std::vector<Prod> prods;
     std::vector<const sell_matrix *> owner;
-    std::vector<std::pair<int64_t, int32_t>> order;  // (stored elements, product) for ordering
     for (int32_t i = 0; i < n; ++i) {
         const sell_batch_item &it = items[i];
         const sell_matrix *h = it.A;
@@ -118,6 +124,7 @@ sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s
             return fail(SELL_EINVAL, "sell_batch_create: unsupported flags");
         if ((it.flags & SELL_SPMV_COMPENSATED) && h->store_type == SELL_F64)
             return fail(SELL_EUNSUPPORTED, "compensated accumulation needs F32/BF16 storage");
+        if (h->nrows == 0) continue;
         const size_t xs = h->store_type == SELL_F64 ? 8 : 4;
         for (int32_t done = 0; done < it.k;) {
             int rem = it.k - done;
@@ -142,21 +149,13 @@ sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s
             P.kb = kb;
             P.type = h->store_type;
             P.acc = (it.flags & SELL_SPMV_ACCUMULATE) ? 1 : 0;
-            P.comp = (it.flags & SELL_SPMV_COMPENSATED) ? 1 : 0;
+            P.comp = (it.flags & SELL_SPMV_COMPENSATED) && h->store_type != SELL_F64 ? 1 : 0;
             P.vec = (((uintptr_t)P.X % 16) == 0 && ((it.ldx * xs) % 16) == 0) ? 1 : 0;
-            if (h->nrows > 0) {
-                order.push_back({h->stored * kb, (int32_t)prods.size()});
-                prods.push_back(P);
-                owner.push_back(h);
-            }
+            prods.push_back(P);
+            owner.push_back(h);
             done += kb;
         }
     }
-    // biggest products first: their tiles start early and small ones fill the tail
-    std::stable_sort(order.begin(), order.end(),
-                     [](const std::pair<int64_t, int32_t> &a, const std::pair<int64_t, int32_t> &b) {
-                         return a.first > b.first;
-                     });
     // each product with long rows gets its own segment scratch and counters,
     // so products of one plan (even on the same matrix) never share them
     b->al = current_allocator();
@@ -172,50 +171,91 @@ sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s
         prods[i].part = p;
         prods[i].cnt = static_cast<int32_t *>(c);
     }
-    // long-row work first (its units are the longest), then row tiles
-    std::vector<Unit> units;
-    for (auto &o : order) {
-        const Prod &P = prods[o.second];
-        for (int64_t v0 = 0; v0 < P.long_threads; v0 += kTileRows) units.push_back({o.second, 1, v0});
-    }
-    for (auto &o : order) {
-        const Prod &P = prods[o.second];
-        for (int64_t r0 = 0; r0 < P.N; r0 += kTileRows) units.push_back({o.second, 0, r0});
-    }
-    b->nprod = (int32_t)prods.size();
-    b->nwork = (int64_t)units.size();
-    DevBuf dp, du, dc;
-    if (!prods.empty()) {
-        SELL_TRY(dp.alloc(b->al, prods.size() * sizeof(Prod), s));
-        SELL_TRY(du.alloc(b->al, units.size() * sizeof(Unit), s));
-        SELL_CUDA_TRY(cudaMemcpyAsync(dp.p, prods.data(), prods.size() * sizeof(Prod),
-                                      cudaMemcpyHostToDevice, s));
-        SELL_CUDA_TRY(cudaMemcpyAsync(du.p, units.data(), units.size() * sizeof(Unit),
-                                      cudaMemcpyHostToDevice, s));
-    }
-    SELL_TRY(dc.alloc(b->al, sizeof(unsigned int), s));
-    SELL_CUDA_TRY(cudaStreamSynchronize(s));
-    int dev = 0, sms = 0, occ = 0;
+    // group by kernel variant; inside a group: long-row work first, biggest first
+    std::map<std::tuple<int, int, int>, std::vector<int32_t>> groups;
+    for (size_t i = 0; i < prods.size(); ++i)
+        groups[std::make_tuple(prods[i].type, prods[i].comp, prods[i].kb)].push_back((int32_t)i);
+    int dev = 0;
     SELL_CUDA_TRY(cudaGetDevice(&dev));
-    SELL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    SELL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch, kTileRows, 0));
     b->device = dev;
-    b->grid_default = std::max(1, sms * std::max(occ, 1));
-    b->items = dp.release_ownership();
-    b->units = du.release_ownership();
-    b->counter = static_cast<unsigned int *>(dc.release_ownership());
+    b->nprod = (int32_t)prods.size();
+    b->nwork = 0;
+    std::vector<std::pair<int64_t, int>> order;  // (work, group index) biggest group first
+    std::vector<std::vector<Prod>> gp;
+    std::vector<std::vector<Unit>> gu;
+    std::vector<std::tuple<int, int, int>> gkey;
+    for (auto &kv : groups) {
+        std::vector<int32_t> ids = kv.second;
+        std::stable_sort(ids.begin(), ids.end(), [&](int32_t a, int32_t c) {
+            return owner[a]->stored > owner[c]->stored;
+        });
+        std::vector<Prod> pv;
+        std::vector<Unit> uv;
+        for (int32_t id : ids) pv.push_back(prods[id]);
+        for (size_t j = 0; j < pv.size(); ++j)
+            for (int64_t v0 = 0; v0 < pv[j].long_threads; v0 += kTileRows) uv.push_back({(int32_t)j, 1, v0});
+        for (size_t j = 0; j < pv.size(); ++j)
+            for (int64_t r0 = 0; r0 < pv[j].N; r0 += kTileRows) uv.push_back({(int32_t)j, 0, r0});
+        int64_t work = 0;
+        for (auto &p : pv) work += owner[0] ? p.N * p.kb : 0;
+        order.push_back({work, (int)gp.size()});
+        gp.push_back(std::move(pv));
+        gu.push_back(std::move(uv));
+        gkey.push_back(kv.first);
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [](const std::pair<int64_t, int> &a, const std::pair<int64_t, int> &c) { return a.first > c.first; });
+    for (auto &o : order) {
+        const int g = o.second;
+        // launches of at most kLaunchProds products each
+        KernelFn fn = kernel_for(std::get<0>(gkey[g]), std::get<1>(gkey[g]), std::get<2>(gkey[g]));
+        for (size_t p0 = 0; p0 < gp[g].size(); p0 += kLaunchProds) {
+            const size_t p1 = std::min(gp[g].size(), p0 + (size_t)kLaunchProds);
+            std::vector<Unit> uv;
+            for (const Unit &u : gu[g])
+                if ((size_t)u.prod >= p0 && (size_t)u.prod < p1) uv.push_back({u.prod - (int32_t)p0, u.kind, u.idx});
+            if (uv.empty()) continue;
+            DevBuf du;
+            SELL_TRY(du.alloc(b->al, uv.size() * sizeof(Unit), s));
+            SELL_CUDA_TRY(cudaMemcpyAsync(du.p, uv.data(), uv.size() * sizeof(Unit), cudaMemcpyHostToDevice, s));
+            SELL_CUDA_TRY(cudaStreamSynchronize(s));  // uv goes out of scope below
+            auto *lp = new (std::nothrow) LaunchParams();
+            if (!lp) return fail(SELL_ENOMEM, "sell_batch_create: host allocation failed");
+            for (size_t j = p0; j < p1; ++j) lp->prods[j - p0] = gp[g][j];
+            lp->units = static_cast<const Unit *>(du.p);
+            lp->nwork = (int64_t)uv.size();
+            sell_batch::Group G;
+            G.fn = reinterpret_cast<void *>(fn);
+            G.params = lp;
+            G.nwork = lp->nwork;
+            G.grid = (int32_t)std::min<int64_t>(G.nwork, 0x7FFFFFFF);  // one block per unit
+            G.units = du.release_ownership();
+            b->groups.push_back(G);
+            b->nwork += G.nwork;
+        }
+    }
     return SELL_OK;
 }
 
+void batch_release(sell_batch *b, cudaStream_t s) {
+    for (auto &G : b->groups) {
+        b->al.put(G.units, s);
+        delete static_cast<LaunchParams *>(G.params);
+    }
+    b->groups.clear();
+    for (void *p : b->scratch) b->al.put(p, s);
+    b->scratch.clear();
+}
+
 sell_status batch_run(sell_batch *b, int32_t grid, cudaStream_t s) {
+    if (grid != 0) return fail(SELL_EINVAL, "sell_batch_run: grid must be 0 (one block per work unit)");
     b->last_stream = s;
     b->ran = true;
-    if (b->nwork == 0) return SELL_OK;
-    int g = grid > 0 ? grid : b->grid_default;
-    SELL_CUDA_TRY(cudaMemsetAsync(b->counter, 0, sizeof(unsigned int), s));
-    k_batch<<<g, kTileRows, 0, s>>>(static_cast<const Prod *>(b->items),
-                                    static_cast<const Unit *>(b->units), b->nwork, b->counter);
-    SELL_CUDA_TRY(cudaGetLastError());
+    for (const sell_batch::Group &G : b->groups) {
+        KernelFn fn = reinterpret_cast<KernelFn>(G.fn);
+        fn<<<G.grid, kTileRows, 0, s>>>(*static_cast<const LaunchParams *>(G.params));
+        SELL_CUDA_TRY(cudaGetLastError());
+    }
     return SELL_OK;
 }
 

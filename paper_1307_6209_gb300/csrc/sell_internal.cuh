@@ -94,15 +94,19 @@ struct sell_matrix {
 };
 
 struct sell_batch {
+    struct Group {              // one launch: kernel variant, its products and units
+        void *fn = nullptr;     // kernel entry
+        void *params = nullptr; // host copy of the launch parameters (products + unit table pointer)
+        void *units = nullptr;  // device work-unit table
+        int64_t nwork = 0;
+        int32_t grid = 0;
+    };
     int device = 0;
     sell::Allocator al;
     std::vector<void *> scratch;  // per-product segment scratch and counters
-    void *items = nullptr;      // device product table
-    void *units = nullptr;      // device work-unit table
-    unsigned int *counter = nullptr;
+    std::vector<Group> groups;
     int64_t nwork = 0;
     int32_t nprod = 0;
-    int32_t grid_default = 0;
     cudaStream_t last_stream = nullptr;  // stream of the latest sell_batch_run
     bool ran = false;
 };
@@ -119,6 +123,7 @@ sell_status launch_block_with_scratch(const sell_matrix *h, const void *X, int64
 sell_status build_format(const sell_csr *A, const sell_opts *o, cudaStream_t s, sell_matrix *h);
 sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s, sell_batch *b);
 sell_status batch_run(sell_batch *b, int32_t grid, cudaStream_t s);
+void batch_release(sell_batch *b, cudaStream_t s);
 sell_status bench_read(const void *buf, size_t bytes, double *sink, int32_t grid, cudaStream_t s);
 sell_status bench_fma64(double *sink, int32_t grid, int32_t iters, cudaStream_t s);
 sell_status bench_gather(const void *x, int64_t n, double *sink, int32_t grid, int32_t iters, cudaStream_t s);

@@ -10,7 +10,8 @@ that arrive while others run on the GPU are admitted as soon as a stream and
 memory are free, and their work overlaps on the device.  Each result is
 bitwise the same as the request run alone (the per-row arithmetic does not
 depend on the batch).  Latency is measured from arrival to the moment the
-result is back in host memory.
+result is back in host memory (or, for requests whose result stays on the
+device, to the completion of the batch on the GPU).
 """
 from __future__ import annotations
 
@@ -33,9 +34,10 @@ class Request:
     t_arrive: float
     t_launch: float = 0.0
     t_done: float = 0.0
-    Y: object = None           # pinned host tensor, nrows x k
+    Y: object = None           # result: pinned host tensor, or device tensor (to_host=False)
     done: threading.Event = field(default_factory=threading.Event)
     nbytes: int = 0
+    to_host: bool = True
 
     @property
     def latency(self) -> float:
@@ -78,10 +80,13 @@ class Server:
         es = 8 if inf.store_type == sell.SELL_F64 else 4
         return (inf.ncols + inf.nrows) * k * es
 
-    def submit(self, mid: int, X) -> Request:
+    def submit(self, mid: int, X, to_host: bool = True) -> Request:
+        """Queue Y = A_mid X.  X is a pinned host tensor (ncols, or ncols x k);
+        the result comes back to pinned host memory, or stays on the device
+        (to_host=False) for a consumer that works there."""
         k = 1 if X.dim() == 1 else int(X.shape[1])
         with self.cv:
-            r = Request(self._rid, mid, X, k, time.perf_counter())
+            r = Request(self._rid, mid, X, k, time.perf_counter(), to_host=to_host)
             r.nbytes = self.request_bytes(mid, k)
             if self.resident + r.nbytes > self.budget:
                 raise ValueError("request larger than the HBM budget")
@@ -136,8 +141,11 @@ class Server:
         plan.run(stream=s)
         with torch.cuda.stream(s):
             for r, Xd, Yd in bufs:
-                r.Y = torch.empty(Yd.shape, dtype=Yd.dtype, pin_memory=True)
-                r.Y.copy_(Yd, non_blocking=True)
+                if r.to_host:
+                    r.Y = torch.empty(Yd.shape, dtype=Yd.dtype, pin_memory=True)
+                    r.Y.copy_(Yd, non_blocking=True)
+                else:
+                    r.Y = Yd
             ev = torch.cuda.Event()
             ev.record(s)
         self.inflight.append((si, ev, bufs, plan))
@@ -198,7 +206,8 @@ class Server:
                 "budget_bytes": int(self.budget)}
 
 
-def poisson_load(server: Server, rate_hz: float, duration_s: float, make_request, seed: int = 0):
+def poisson_load(server: Server, rate_hz: float, duration_s: float, make_request, seed: int = 0,
+                 to_host: bool = True):
     """Submit requests with exponential inter-arrival times for duration_s;
     make_request(rng) -> (mid, pinned X).  Returns the submitted requests."""
     rng = np.random.default_rng(seed)
@@ -215,5 +224,5 @@ def poisson_load(server: Server, rate_hz: float, duration_s: float, make_request
                 break
             time.sleep(min(t_next - now, 1e-4))
         mid, X = make_request(rng)
-        reqs.append(server.submit(mid, X))
+        reqs.append(server.submit(mid, X, to_host=to_host))
     return reqs

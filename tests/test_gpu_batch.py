@@ -41,10 +41,10 @@ def test_batch_equals_alone():
         sell.sell_spmmv(h, X, Ya, flags=fl)
         alone.append(Ya)
     plan = sell.sell_batch_create(prods)
-    for grid in (0, 1, 7):
+    for rep in range(3):
         for _, _, Y, _ in prods:
             Y.fill_(float("nan"))
-        plan.run(grid=grid)
+        plan.run()
         torch.cuda.synchronize()
         for (h, X, Y, fl), Ya in zip(prods, alone):
             assert Y.cpu().numpy().tobytes() == Ya.cpu().numpy().tobytes()
@@ -77,4 +77,10 @@ def test_batch_empty_and_bad_items():
     from paper_1307_6209_gb300 import sell
     plan = sell.sell_batch_create([])
     plan.run()
+    plan.free()
+    prods = _make_products(seed=3, n=2)
+    plan = sell.sell_batch_create(prods)
+    with pytest.raises(sell.SellError) as e:
+        plan.run(grid=5)
+    assert e.value.status == sell.SELL_EINVAL
     plan.free()

@@ -59,7 +59,7 @@ def test_results_alone_equal_in_the_mix():
     for burst in range(6):
         for _ in range(int(rng.integers(5, 30))):
             mid, X = _make(mats, rng)
-            reqs.append(srv.submit(mid, X))
+            reqs.append(srv.submit(mid, X, to_host=bool(rng.random() < 0.7)))
         time.sleep(0.002)
     for r in reqs:
         assert r.done.wait(60)
@@ -68,7 +68,8 @@ def test_results_alone_equal_in_the_mix():
     assert st["requests"] == len(reqs) and st["batches"] >= 2
     for r in reqs:
         ref = _alone(mats[r.mid], r.X)
-        assert r.Y.numpy().tobytes() == ref.numpy().tobytes(), f"request {r.rid} differs"
+        got = r.Y.cpu() if r.Y.is_cuda else r.Y
+        assert got.numpy().tobytes() == ref.numpy().tobytes(), f"request {r.rid} differs"
 
 
 def test_budget_is_respected_and_everything_completes():
