@@ -143,3 +143,35 @@ def build_tuned(A, choice: Choice, store_type: int = sell.SELL_F64, stream=None)
     h = sell.sell_build(A, C=choice.C, sigma=choice.sigma, store_type=store_type, stream=stream)
     sell.sell_set_launch(h, choice.block, choice.unroll)
     return h
+
+
+def tune_batch(samples, store_type: int = sell.SELL_F32, Cs=(32, 64), sigmas=(1, 32, 256, 4096, 1 << 30),
+               reps: int = 10, stream=None):
+    """Pick (C, sigma) for a class of matrices by the throughput of a batch.
+
+    Each candidate builds every sample matrix and times one persistent batch
+    (sell_batch_create / sell_batch_run) over all of them.  A single small
+    matrix is latency-bound and would favour formats that move more bytes;
+    in a batch, the bytes count: with unsorted chunks the row-length skip
+    saves instructions but not DRAM sectors, so the padding of Eq. "beta" is
+    read anyway.  Returns (best {"C", "sigma", "us"}, list of all candidates).
+    """
+    import torch
+
+    stream = stream or torch.cuda.current_stream()
+    dt = torch.float64 if store_type == sell.SELL_F64 else torch.float32
+    best, table = None, []
+    for C in Cs:
+        for sg in sigmas:
+            hs = [sell.sell_build(A, C=C, sigma=sg, store_type=store_type, stream=stream) for A in samples]
+            items = [(h, torch.rand(h.info.ncols, dtype=dt, device="cuda"),
+                      torch.empty(h.info.nrows, dtype=dt, device="cuda"), 0) for h in hs]
+            plan = sell.sell_batch_create(items, stream=stream)
+            us = _time(lambda: plan.run(stream=stream), stream, reps)
+            table.append({"C": C, "sigma": sg, "us": us})
+            if best is None or us < best["us"]:
+                best = {"C": C, "sigma": sg, "us": us}
+            plan.free()
+            for h in hs:
+                h.free()
+    return best, table
