@@ -38,7 +38,8 @@ if ROOT not in sys.path:
 
 L2_BYTES = 129 * 2 ** 20
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SOURCES = ["paper_1307_6209_gb300/csrc/sell_spmv.cu", "paper_1307_6209_gb300/csrc/sell_internal.cuh"]
+KERNEL_SOURCES = ["paper_1307_6209_gb300/csrc/sell_spmv.cu", "paper_1307_6209_gb300/csrc/sell_internal.cuh",
+                  "paper_1307_6209_gb300/csrc/sell_rowdot.cuh"]
 
 
 def parse_args():
@@ -546,6 +547,7 @@ def run_ours(args):
     import torch
     from paper_1307_6209_gb300 import autotune
     from paper_1307_6209_gb300 import build as cuda_build
+    from paper_1307_6209_gb300 import dist as sdist
     from paper_1307_6209_gb300 import model, sell
 
     ws, rank, local = dist_setup()
@@ -618,13 +620,10 @@ def run_ours(args):
         clk.stop()
         total_s = t_start.elapsed_time(t_end) * 1e-3
         kern_s = sum(a.elapsed_time(b) for a, b in zip(ev_a, ev_b)) * 1e-3 / args.steps
-        if dist:
-            t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_s = float(t.item())
-        step_s = total_s / args.steps
         flops = 2.0 * A.nnz
-        value = n_gpus * flops / step_s / 1e9
+        # weak scaling: every rank's flops over the slowest rank's time
+        value = sdist.weak_scaling_throughput(flops * args.steps, total_s, device="cuda") / 1e9
+        step_s = sdist.max_over_ranks(total_s, device="cuda") / args.steps
 
         extras = {}
         e2e = None

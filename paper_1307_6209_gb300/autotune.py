@@ -149,7 +149,7 @@ def tune_batch(samples, store_type: int = sell.SELL_F32, Cs=(32, 64), sigmas=(1,
                reps: int = 10, stream=None):
     """Pick (C, sigma) for a class of matrices by the throughput of a batch.
 
-    Each candidate builds every sample matrix and times one persistent batch
+    Each candidate builds every sample matrix and times one batched launch
     (sell_batch_create / sell_batch_run) over all of them.  A single small
     matrix is latency-bound and would favour formats that move more bytes;
     in a batch, the bytes count: with unsorted chunks the row-length skip

@@ -1,0 +1,99 @@
+"""The multi-process paths on CPU ranks (gloo, world size 2).
+
+* Weak scaling (what bench.py does under torchrun): the job throughput is the
+  sum of the ranks' work over the slowest rank's time.
+* Row sharding of one matrix: the ranks' formats are exactly the pieces of
+  the global format (no sorting window or chunk crosses a boundary), and after
+  one allgather of x each rank's rows give the global product bit for bit.
+"""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, results):
+    import torch.distributed as dist
+
+    import oracle
+    from paper_1307_6209_gb300 import dist as sdist
+    from paper_1307_6209_gb300 import synth
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), WORLD_SIZE=str(world), RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        out = {}
+        # weak scaling: units (100, 200) over max time (1.5 s)
+        out["tp"] = sdist.weak_scaling_throughput(100.0 * (rank + 1), 0.5 + rank)
+
+        # row sharding of one matrix
+        A = synth.lognormal(5003, seed=4, cap=400)
+        x = synth.vector(A.ncols, seed=5)
+        C, sigma = 32, 256
+        bounds = sdist.shard_rows(A.nrows, sigma, C, world, rpt=A.rpt)
+        r0, r1 = bounds[rank]
+        S = synth.CSR(r1 - r0, A.ncols, A.rpt[r0:r1 + 1] - A.rpt[r0], A.col[A.rpt[r0]:A.rpt[r1]],
+                      A.val[A.rpt[r0]:A.rpt[r1]])
+        Fs = oracle.sell_build(S, C, sigma)
+        F = oracle.sell_build(A, C, sigma)
+        c0, c1 = r0 // C, r0 // C + Fs["nchunks"]
+        out["pieces"] = bool(
+            np.array_equal(Fs["cs"], F["cs"][c0:c1 + 1] - F["cs"][c0])
+            and Fs["val"].tobytes() == F["val"][F["cs"][c0]:F["cs"][c1]].tobytes()
+            and np.array_equal(Fs["col"], F["col"][F["cs"][c0]:F["cs"][c1]])
+            and np.array_equal(Fs["perm"] + r0, F["perm"][r0:r1]))
+
+        # one allgather of x (each rank owns the slice matching its rows)
+        mine = torch.from_numpy(x[r0:r1].copy())
+        width = max(b - a for a, b in bounds)
+        pad = torch.zeros(width, dtype=torch.float64)
+        pad[:mine.numel()] = mine
+        parts = [torch.empty(width, dtype=torch.float64) for _ in range(world)]
+        dist.all_gather(parts, pad)
+        xg = torch.cat([p[:b - a] for p, (a, b) in zip(parts, bounds)]).numpy()
+        y_local = oracle.sell_spmv(Fs, xg)
+        ypad = torch.zeros(width, dtype=torch.float64)
+        ypad[:y_local.shape[0]] = torch.from_numpy(y_local)
+        yparts = [torch.empty(width, dtype=torch.float64) for _ in range(world)]
+        dist.all_gather(yparts, ypad)
+        y = torch.cat([p[:b - a] for p, (a, b) in zip(yparts, bounds)]).numpy()
+        out["y_equal"] = y.tobytes() == oracle.csr_spmv(A, x).tobytes()
+        out["bounds"] = bounds
+        results[rank] = out
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_gloo():
+    import torch.multiprocessing as mp
+    world = 2
+    port = _free_port()
+    with mp.Manager() as m:
+        results = m.dict()
+        mp.spawn(_worker, args=(world, port, results), nprocs=world, join=True)
+        res = dict(results)
+    for r in range(world):
+        assert res[r]["tp"] == pytest.approx(200.0)
+        assert res[r]["pieces"], f"rank {r}: shard format is not a piece of the global format"
+        assert res[r]["y_equal"], f"rank {r}: sharded product differs"
+    b = res[0]["bounds"]
+    assert b[0][0] == 0 and b[-1][1] == 5003 and all(x % 256 == 0 for x, _ in b)
+
+
+def test_shard_rows_alignment():
+    from paper_1307_6209_gb300 import dist as sdist
+    for n, sigma, C, w in [(10000, 256, 32, 3), (1000, 1, 32, 4), (777, 10 ** 9, 64, 2), (0, 1, 32, 2)]:
+        b = sdist.shard_rows(n, sigma, C, w)
+        assert b[0][0] == 0 and b[-1][1] == n and len(b) == w
+        step = np.lcm(max(1, min(sigma, n) if n else 1), C)
+        assert all(a <= c for (a, c) in b)
+        assert all(a % step == 0 or a == n for a, _ in b)
