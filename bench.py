@@ -543,6 +543,36 @@ def serving_section(sell, stream, nmat=64, seed=0, duration_s=1.5):
     return out
 
 
+def pathological_section(sell, model, stream, peak):
+    """The shapes Sec. 5.2 singles out for accelerators: a dense 8000 x 8000
+    matrix stored as sparse (few rows, long rows; the paper quotes 7.3 / 23 /
+    17 GF/s on SNB / Phi / K20 and 31 GF/s on K20 with 16 threads per row) and
+    a webbase-1M-like matrix (1M rows of 3 entries plus one row of 1M)."""
+    import torch
+    from paper_1307_6209_gb300 import synth
+    out = {}
+    cases = (("dense8000", lambda: synth.dense_device(8000), ((32, 1),)),
+             ("webbase_like_1M", lambda: synth.long_row_device(1_000_000, 1_000_000, short_len=3, at=12345),
+              ((32, 1), (32, 1 << 30))))
+    for name, make, fmts in cases:
+        A = make()
+        x = torch.rand(A.ncols, dtype=torch.float64, device="cuda")
+        y = torch.empty(A.nrows, dtype=torch.float64, device="cuda")
+        for C, sg in fmts:
+            h = sell.sell_build(A, C=C, sigma=sg, stream=stream)
+            blk, unr, _ = tune_launch(sell, h, x, y, stream)
+            dt = time_spmv(sell, h, x, y, stream, reps=50)
+            alg = model.algorithmic_bytes(A.nrows, A.ncols, A.nnz, h.info.nchunks, C, 8, 8, h.info.has_perm)
+            out[f"{name}_C{C}_s{sg}"] = {"nnz": A.nnz, "us": round(dt * 1e6, 2),
+                                          "gflops": round(2.0 * A.nnz / dt / 1e9, 1),
+                                          "hbm_frac": round(alg / dt / 1e9 / peak, 4), "beta": round(h.info.beta, 4),
+                                          "block": blk, "unroll": unr}
+            h.free()
+        del A, x, y
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_1307_6209_gb300 import autotune
@@ -680,6 +710,7 @@ def run_ours(args):
         torch.cuda.empty_cache()
         if not args.no_extras and args.workload == "lognormal" and rank == 0:
             extras["stencil27"] = stencil_section(sell, model, stream, peak, fma_tf)
+            extras["pathological"] = pathological_section(sell, model, stream, peak)
             extras["batched"] = batched_section(sell, autotune, stream)
             extras["serving"] = serving_section(sell, stream)
 

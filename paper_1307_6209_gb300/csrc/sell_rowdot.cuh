@@ -217,7 +217,22 @@ __device__ __forceinline__ void long_unit(const VT *__restrict__ val, const int3
     Acc tot[K];
 #pragma unroll
     for (int q = 0; q < K; ++q) tot[q] = Acc::load_l2(part + (u0 * C + l) * K + q);
-    for (int s2 = 1; s2 < nseg; ++s2) {
+    // the partials are loaded FB segments at a time (independent loads in
+    // flight) and folded in segment order
+    constexpr int FB = K >= 8 ? 2 : (K >= 4 ? 4 : 16 / K);
+    int s2 = 1;
+    for (; s2 + FB <= nseg; s2 += FB) {
+        Acc buf[FB][K];
+#pragma unroll
+        for (int f = 0; f < FB; ++f)
+#pragma unroll
+            for (int q = 0; q < K; ++q) buf[f][q] = Acc::load_l2(part + ((u0 + s2 + f) * C + l) * K + q);
+#pragma unroll
+        for (int f = 0; f < FB; ++f)
+#pragma unroll
+            for (int q = 0; q < K; ++q) tot[q].merge(buf[f][q]);
+    }
+    for (; s2 < nseg; ++s2) {
 #pragma unroll
         for (int q = 0; q < K; ++q) tot[q].merge(Acc::load_l2(part + ((u0 + s2) * C + l) * K + q));
     }

@@ -312,3 +312,33 @@ def banded_device(N: int, bandwidth: int = 64, lo: int = 7, hi: int = 30, seed: 
     rpt = torch.zeros(N + 1, dtype=torch.int64, device=device)
     torch.cumsum(rl, 0, out=rpt[1:])
     return CSR(N, N, rpt, col.to(torch.int32), val)
+
+
+def dense_device(n: int, m: int | None = None, seed: int = 0, device: str = "cuda") -> CSR:
+    """A dense n x m matrix stored as CSR on the device (values N(0,1))."""
+    import torch
+    m = n if m is None else m
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    rpt = torch.arange(n + 1, device=device, dtype=torch.int64) * m
+    col = torch.arange(m, device=device, dtype=torch.int32).repeat(n)
+    val = torch.randn(n * m, generator=g, device=device, dtype=torch.float64)
+    return CSR(n, m, rpt, col, val)
+
+
+def long_row_device(N: int, long_len: int, short_len: int = 3, at: int = 0, seed: int = 0,
+                    device: str = "cuda") -> CSR:
+    """Short rows of ``short_len`` distinct random columns plus one row of
+    ``long_len`` (a webbase-1M-like profile: the paper's Sec. 5.2 cites one
+    row of 1,000,005 entries against a mean of 3.11), on the device."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    rl = torch.full((N,), min(short_len, N), dtype=torch.int64, device=device)
+    rl[at] = min(long_len, N)
+    col = _distinct_sorted_columns_device(rl, torch.zeros(N, dtype=torch.int64, device=device),
+                                          torch.full((N,), N, dtype=torch.int64, device=device), g)
+    val = torch.randn(col.shape[0], generator=g, device=device, dtype=torch.float64)
+    rpt = torch.zeros(N + 1, dtype=torch.int64, device=device)
+    torch.cumsum(rl, 0, out=rpt[1:])
+    return CSR(N, N, rpt, col.to(torch.int32), val)

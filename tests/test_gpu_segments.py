@@ -40,7 +40,7 @@ def _row_result(vals, xs, y0):
 
 
 def _matrix():
-    lens = [0, 1, 5, 63, 64, 65, 100, 127, 128, 129, 192, 200, 257, 640, 1000, 3]
+    lens = [0, 1, 5, 63, 64, 65, 100, 127, 128, 129, 192, 200, 257, 640, 1000, 3, 1500, 2000, 1089]
     rng = np.random.default_rng(42)
     n = 2048
     rows = []

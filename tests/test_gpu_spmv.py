@@ -126,3 +126,26 @@ def test_spmv_empty_matrix_is_noop():
     sell.sell_spmv(h, torch.empty(0, dtype=torch.float64, device="cuda"),
                    torch.empty(0, dtype=torch.float64, device="cuda"))
     assert h.info.stored == 0 and h.info.nchunks == 0
+
+
+@pytest.mark.parametrize("shape", ["dense", "one_long_row", "many_long_rows"])
+def test_spmv_very_long_rows(shape):
+    """Rows of hundreds of 64-entry segments (folded in batches plus a
+    remainder) against the oracle, bitwise invariant over (C, sigma)."""
+    from paper_1307_6209_gb300 import sell
+    if shape == "dense":
+        A = synth.dense(300, 2500, seed=1)            # 40 segments per row
+    elif shape == "one_long_row":
+        A = synth.long_row(30000, 30000, short_len=3, at=777, seed=2)  # 469 segments
+    else:
+        A = synth.lognormal(3000, mean=900.0, sigma_ln=0.5, cap=3000, seed=3)
+    x = synth.vector(A.ncols, seed=4)
+    ref, scale, rl = oracle_reference(A, x)
+    first = None
+    for C, sigma in [(32, 1), (64, 10 ** 9), (7, 100)]:
+        h = sell.sell_build(A, C=C, sigma=sigma)
+        y = _spmv(h, x)
+        assert np.all(np.abs(y - ref) <= tol_f64(rl, scale)), (C, sigma)
+        first = y if first is None else first
+        assert y.tobytes() == first.tobytes()
+        h.free()
