@@ -114,22 +114,39 @@ def lognormal_lengths(N: int, mean: float = 16.0, sigma_ln: float = 1.2, cap: in
 
 def _distinct_sorted_columns(rl: np.ndarray, lo: np.ndarray, hi: np.ndarray, rng) -> np.ndarray:
     """For every row i draw rl[i] distinct integers uniformly from [lo[i], hi[i]),
-    sorted ascending; rows are concatenated in row order."""
+    sorted ascending; rows are concatenated in row order.  Rows that need more
+    than a quarter of their span are drawn without replacement one by one;
+    the others by drawing with replacement and redrawing duplicates."""
     N = rl.shape[0]
-    rows = np.repeat(np.arange(N, dtype=np.int64), rl)
-    span = (hi - lo)[rows]
-    base = lo[rows]
-    width = int(max(1, (hi - lo).max(initial=1)))
-    cols = base + rng.integers(0, np.iinfo(np.int64).max, rows.shape[0]) % span
-    while True:
-        key = rows * width + (cols - base)
-        order = np.argsort(key, kind="stable")
-        ks = key[order]
-        dup = np.nonzero(ks[1:] == ks[:-1])[0] + 1
-        if dup.size == 0:
-            return cols[order]
-        at = order[dup]
-        cols[at] = base[at] + rng.integers(0, np.iinfo(np.int64).max, at.shape[0]) % span[at]
+    out = np.empty(int(rl.sum()), np.int64)
+    start = np.zeros(N + 1, np.int64)
+    np.cumsum(rl, out=start[1:])
+    full = rl > np.maximum(hi - lo, 1) // 4
+    for i in np.nonzero(full)[0]:
+        out[start[i]:start[i + 1]] = lo[i] + np.sort(rng.choice(int(hi[i] - lo[i]), size=int(rl[i]),
+                                                                replace=False))
+    sparse_rows = np.nonzero(~full)[0]
+    if sparse_rows.size:
+        rls = rl[sparse_rows]
+        rows = np.repeat(np.arange(sparse_rows.size, dtype=np.int64), rls)
+        span = (hi - lo)[sparse_rows][rows]
+        base = lo[sparse_rows][rows]
+        width = int(max(1, (hi - lo)[sparse_rows].max(initial=1)))
+        cols = base + rng.integers(0, np.iinfo(np.int64).max, rows.shape[0]) % span
+        while True:
+            key = rows * width + (cols - base)
+            order = np.argsort(key, kind="stable")
+            ks = key[order]
+            dup = np.nonzero(ks[1:] == ks[:-1])[0] + 1
+            if dup.size == 0:
+                cols = cols[order]
+                break
+            at = order[dup]
+            cols[at] = base[at] + rng.integers(0, np.iinfo(np.int64).max, at.shape[0]) % span[at]
+        pos = np.repeat(start[sparse_rows], rls) + (np.arange(rows.shape[0]) - np.repeat(
+            np.concatenate([[0], np.cumsum(rls)[:-1]]), rls))
+        out[pos] = cols
+    return out
 
 
 def lognormal(N: int, mean: float = 16.0, sigma_ln: float = 1.2, cap: int = 2000,
@@ -254,28 +271,48 @@ def stencil27_device(n: int, perturb: float = 0.1, seed: int = 0, device: str = 
 
 def _distinct_sorted_columns_device(rl, lo, hi, gen):
     """Device version of _distinct_sorted_columns (torch): rl[i] distinct
-    integers uniform in [lo[i], hi[i]) per row, sorted, rows concatenated."""
+    integers uniform in [lo[i], hi[i]) per row, sorted, rows concatenated.
+    Rows that need more than a quarter of their span are drawn by a random
+    permutation one by one; the others with replacement plus redraws."""
     import torch
     dev = rl.device
     N = rl.shape[0]
-    rows = torch.repeat_interleave(torch.arange(N, device=dev, dtype=torch.int64), rl)
-    span = (hi - lo)[rows]
-    base = lo[rows]
-    width = int(max(1, int((hi - lo).max()))) if N else 1
+    start = torch.zeros(N + 1, dtype=torch.int64, device=dev)
+    torch.cumsum(rl, 0, out=start[1:])
+    out = torch.empty(int(start[-1]), dtype=torch.int64, device=dev)
+    spans = torch.clamp(hi - lo, min=1)
+    full = rl > spans // 4
+    for i in torch.nonzero(full, as_tuple=True)[0].tolist():
+        sp = int(spans[i])
+        pick = torch.randperm(sp, generator=gen, device=dev)[:int(rl[i])]
+        out[int(start[i]):int(start[i + 1])] = lo[i] + torch.sort(pick).values
+    keep = torch.nonzero(~full, as_tuple=True)[0]
+    if keep.numel():
+        rls = rl[keep]
+        rows = torch.repeat_interleave(torch.arange(keep.numel(), device=dev, dtype=torch.int64), rls)
+        span = spans[keep][rows]
+        base = lo[keep][rows]
+        width = int(max(1, int(spans[keep].max())))
 
-    def draw(m, sp):
-        r = torch.randint(0, 2 ** 62, (m,), generator=gen, device=dev, dtype=torch.int64)
-        return r % sp
+        def draw(m, sp):
+            r = torch.randint(0, 2 ** 62, (m,), generator=gen, device=dev, dtype=torch.int64)
+            return r % sp
 
-    off = draw(rows.shape[0], span)
-    while True:
-        key = rows * width + off
-        key, order = torch.sort(key)
-        off = off[order]
-        dup = torch.nonzero(key[1:] == key[:-1], as_tuple=True)[0] + 1
-        if dup.numel() == 0:
-            return (base + off)
-        off[dup] = draw(dup.numel(), span[dup])
+        off = draw(rows.shape[0], span)
+        while True:
+            key = rows * width + off
+            key, order = torch.sort(key)
+            off = off[order]
+            dup = torch.nonzero(key[1:] == key[:-1], as_tuple=True)[0] + 1
+            if dup.numel() == 0:
+                break
+            off[dup] = draw(dup.numel(), span[dup])
+        first = torch.zeros(keep.numel() + 1, dtype=torch.int64, device=dev)
+        torch.cumsum(rls, 0, out=first[1:])
+        pos = torch.repeat_interleave(start[keep], rls) + (torch.arange(rows.shape[0], device=dev)
+                                                          - torch.repeat_interleave(first[:-1], rls))
+        out[pos] = base + off
+    return out
 
 
 def lognormal_device(N: int, mean: float = 16.0, sigma_ln: float = 1.2, cap: int = 2000, seed: int = 0,
