@@ -74,7 +74,7 @@ void free_matrix(sell_matrix *h) {
     // every kernel that may still read the arrays must finish first
     (void)cudaDeviceSynchronize();
     void *ptrs[] = {h->val,    h->col,   h->cs,   h->cl,     h->srl,    h->perm,
-                    h->lchunk, h->lunit, h->cnt, h->part, h->xstage, h->ystage};
+                    h->lchunk, h->lunit, h->cnt, h->cnt2, h->part, h->xstage, h->ystage};
     for (void *p : ptrs) h->al.put(p, nullptr);
     (void)cudaDeviceSynchronize();
     delete h;

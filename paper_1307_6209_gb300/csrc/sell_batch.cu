@@ -38,6 +38,7 @@ struct Prod {
     const int2 *lunit;
     void *part;    // this product's own segment scratch (owned by the plan)
     int32_t *cnt;  // this product's own segment counters (owned by the plan)
+    int32_t *cnt2; // this product's own group counters (owned by the plan)
     const void *X;
     void *Y;
     int64_t ldx, ldy, N, long_threads;
@@ -79,7 +80,8 @@ k_batch(const __grid_constant__ LaunchParams lp) {
         const int64_t v = u.idx + threadIdx.x;
         if (v < P.long_threads)
             long_unit<VT, XT, K, U, Acc>(static_cast<const VT *>(P.val), P.col, P.cs, P.srl, P.perm, P.lchunk,
-                                         P.lunit, static_cast<Acc *>(P.part), P.cnt, static_cast<const XT *>(P.X),
+                                         P.lunit, static_cast<Acc *>(P.part), P.cnt, P.cnt2,
+                                         static_cast<const XT *>(P.X),
                                          P.ldx, static_cast<XT *>(P.Y), P.ldy, P.N, P.C, v, P.acc, P.vec != 0, pol);
         return;
     }
@@ -138,6 +140,7 @@ sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s
             P.lunit = h->lunit;
             P.part = nullptr;
             P.cnt = nullptr;
+            P.cnt2 = nullptr;
             P.long_threads = h->nunits * h->C;
             P.perm = (h->flags & SELL_BUILD_PERMUTE_COLS) ? nullptr : h->perm;
             P.X = static_cast<const char *>(it.X) + done * xs;
@@ -164,12 +167,16 @@ sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s
         if (h->nunits == 0) continue;
         void *p = b->al.get((size_t)h->nunits * h->C * prods[i].kb * 8, s);
         void *c = p ? b->al.get((size_t)h->nlong * h->C * sizeof(int32_t), s) : nullptr;
+        void *c2 = c ? b->al.get((size_t)h->nunits * h->C * sizeof(int32_t), s) : nullptr;
         if (p) b->scratch.push_back(p);
         if (c) b->scratch.push_back(c);
-        if (!p || !c) return fail(SELL_ENOMEM, "sell_batch_create: segment scratch allocation failed");
+        if (c2) b->scratch.push_back(c2);
+        if (!p || !c || !c2) return fail(SELL_ENOMEM, "sell_batch_create: segment scratch allocation failed");
         SELL_CUDA_TRY(cudaMemsetAsync(c, 0, (size_t)h->nlong * h->C * sizeof(int32_t), s));
+        SELL_CUDA_TRY(cudaMemsetAsync(c2, 0, (size_t)h->nunits * h->C * sizeof(int32_t), s));
         prods[i].part = p;
         prods[i].cnt = static_cast<int32_t *>(c);
+        prods[i].cnt2 = static_cast<int32_t *>(c2);
     }
     // group by kernel variant; inside a group: long-row work first, biggest first
     std::map<std::tuple<int, int, int>, std::vector<int32_t>> groups;

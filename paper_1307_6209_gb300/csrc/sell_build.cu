@@ -607,7 +607,7 @@ sell_status build_format(const sell_csr *A, const sell_opts *o, cudaStream_t s, 
         SELL_CUDA_TRY(cudaMemcpyAsync(&nlong, lpos.as<int64_t>() + Nc, sizeof(int64_t),
                                       cudaMemcpyDeviceToHost, s));
     SELL_CUDA_TRY(cudaStreamSynchronize(s));
-    DevBuf lchunk, lnseg, lubase, lunit, cnt, part;
+    DevBuf lchunk, lnseg, lubase, lunit, cnt, cnt2, part;
     int64_t nunits = 0;
     if (nlong > 0) {
         SELL_TRY(lchunk.alloc(al, nlong * sizeof(int32_t), s));
@@ -629,6 +629,8 @@ sell_status build_format(const sell_csr *A, const sell_opts *o, cudaStream_t s, 
         SELL_CUDA_TRY(cudaGetLastError());
         SELL_TRY(cnt.alloc(al, nlong * C * sizeof(int32_t), s));
         SELL_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, nlong * C * sizeof(int32_t), s));
+        SELL_TRY(cnt2.alloc(al, (size_t)nunits * C * sizeof(int32_t), s));
+        SELL_CUDA_TRY(cudaMemsetAsync(cnt2.p, 0, (size_t)nunits * C * sizeof(int32_t), s));
         SELL_TRY(part.alloc(al, (size_t)nunits * C * 8, s));
     }
 
@@ -675,10 +677,11 @@ sell_status build_format(const sell_csr *A, const sell_opts *o, cudaStream_t s, 
     h->nunits = nunits;
     h->part_k = nunits > 0 ? 1 : 0;
     h->device_bytes = val.bytes + col.bytes + cs.bytes + cl.bytes + srl.bytes + perm.bytes + lchunk.bytes +
-                      lunit.bytes + cnt.bytes + part.bytes;
+                      lunit.bytes + cnt.bytes + cnt2.bytes + part.bytes;
     h->lchunk = (int32_t *)lchunk.release_ownership();
     h->lunit = (int2 *)lunit.release_ownership();
     h->cnt = (int32_t *)cnt.release_ownership();
+    h->cnt2 = (int32_t *)cnt2.release_ownership();
     h->part = part.release_ownership();
     h->val = val.release_ownership();
     h->col = (int32_t *)col.release_ownership();

@@ -59,6 +59,9 @@ struct DevBuf {
 // kSeg is summed segment by segment (sell_rowdot.cuh), so changing it changes
 // the rounding of long rows.
 constexpr int kSeg = 64;
+// Segments per group of the two-level fold of very long rows (more than
+// kSeg * kSuper entries); also part of the numerics.
+constexpr int kSuper = 64;
 
 inline size_t value_size(int t) { return t == SELL_F64 ? 8 : (t == SELL_F32 ? 4 : 2); }
 
@@ -85,6 +88,7 @@ struct sell_matrix {
     int2 *lunit = nullptr;     // nunits long-row work units {long chunk, segment}
     int64_t nunits = 0;
     int32_t *cnt = nullptr;    // nlong * C per-row segment counters (zero at rest)
+    int32_t *cnt2 = nullptr;   // nunits * C group counters of very long rows (zero at rest)
     void *part = nullptr;      // segment partials: nunits * C * part_k * 8 bytes
     int32_t part_k = 0;
     // host-io staging (lazily allocated)
@@ -119,7 +123,7 @@ sell_status launch_spmmv(sell_matrix *h, const void *X, int64_t ldx, void *Y, in
                          int32_t k, uint32_t flags, cudaStream_t s);
 sell_status launch_block_with_scratch(const sell_matrix *h, const void *X, int64_t ldx, void *Y,
                                       int64_t ldy, int kb, uint32_t flags, void *part, int32_t *cnt,
-                                      cudaStream_t s);
+                                      int32_t *cnt2, cudaStream_t s);
 sell_status build_format(const sell_csr *A, const sell_opts *o, cudaStream_t s, sell_matrix *h);
 sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s, sell_batch *b);
 sell_status batch_run(sell_batch *b, int32_t grid, cudaStream_t s);

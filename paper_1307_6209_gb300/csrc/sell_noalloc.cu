@@ -63,8 +63,11 @@ extern "C" sell_status sell_spmmv_noalloc(sell_handle h, const void *X, int64_t 
     if (!Y || (!X && h->ncols > 0)) return fail(SELL_EINVAL, "sell_spmmv_noalloc: NULL vector");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
 
-    // scratch layout: [counters: nlong * C int32, padded to 256 B][partials]
-    const size_t cnt_bytes = ((size_t)h->nlong * h->C * sizeof(int32_t) + 255) / 256 * 256;
+    // scratch layout: [row counters: nlong * C int32][group counters: nunits * C
+    // int32][partials], each region padded to 256 bytes
+    const size_t cnt1_bytes = ((size_t)h->nlong * h->C * sizeof(int32_t) + 255) / 256 * 256;
+    const size_t cnt2_bytes = ((size_t)h->nunits * h->C * sizeof(int32_t) + 255) / 256 * 256;
+    const size_t cnt_bytes = cnt1_bytes + cnt2_bytes;
     const size_t per_col = (size_t)h->nunits * h->C * 8;
     int kmax = 8;
     while (kmax > 1 && cnt_bytes + per_col * kmax > kScratchBytes) kmax >>= 1;
@@ -75,6 +78,7 @@ extern "C" sell_status sell_spmmv_noalloc(sell_handle h, const void *X, int64_t 
     void *base = nullptr;
     SELL_TRY(scratch_address(&base));
     int32_t *cnt = static_cast<int32_t *>(base);
+    int32_t *cnt2 = reinterpret_cast<int32_t *>(static_cast<unsigned char *>(base) + cnt1_bytes);
     void *part = static_cast<unsigned char *>(base) + cnt_bytes;
     const size_t xs = h->store_type == SELL_F64 ? 8 : 4;
     for (int32_t done = 0; done < k;) {
@@ -82,9 +86,10 @@ extern "C" sell_status sell_spmmv_noalloc(sell_handle h, const void *X, int64_t 
         int kb = rem >= 8 ? 8 : rem >= 4 ? 4 : rem >= 2 ? 2 : 1;
         while (kb > kmax) kb >>= 1;
         // the array keeps the previous call's contents: counters start at zero
-        if (h->nlong > 0) SELL_CUDA_TRY(cudaMemsetAsync(cnt, 0, (size_t)h->nlong * h->C * sizeof(int32_t), s));
+        if (h->nlong > 0) SELL_CUDA_TRY(cudaMemsetAsync(cnt, 0, cnt_bytes, s));
         SELL_TRY(launch_block_with_scratch(h, static_cast<const char *>(X) + done * xs, ldx,
-                                           static_cast<char *>(Y) + done * xs, ldy, kb, flags, part, cnt, s));
+                                           static_cast<char *>(Y) + done * xs, ldy, kb, flags, part, cnt, cnt2,
+                                           s));
         done += kb;
     }
     return SELL_OK;

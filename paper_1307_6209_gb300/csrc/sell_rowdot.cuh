@@ -10,7 +10,9 @@
 //   L >  kSeg : the row is cut into segments of kSeg consecutive entries;
 //               segment 0 is a chain starting at y0, every other segment a
 //               chain starting at 0; the segment results are then added in
-//               segment order (Dot2: merged with TwoSum, errors carried).
+//               segment order (Dot2: merged with TwoSum, errors carried) --
+//               for more than kSuper segments, first within each group of
+//               kSuper consecutive segments, then the group results in order.
 // Every segment of a long row is an independent work unit, so long rows are
 // spread over the whole grid instead of holding one warp for their full
 // length (Sec. 3.4 notes that one thread per row leaves a warp waiting for
@@ -176,15 +178,49 @@ __device__ __forceinline__ void chain(Acc (&acc)[K], const VT *__restrict__ vp,
     }
 }
 
+// Fold `count` partials of lane l, found at units base, base + stride, ...,
+// in that order (loads issued FB at a time, folds strictly in order).
+template <int K, class Acc>
+__device__ __forceinline__ void fold_partials(const Acc *part, int64_t base, int64_t stride, int count, int C,
+                                              int l, Acc (&tot)[K]) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) tot[q] = Acc::load_l2(part + (base * C + l) * K + q);
+    constexpr int FB = K >= 8 ? 2 : (K >= 4 ? 4 : 16 / K);
+    int i = 1;
+    for (; i + FB <= count; i += FB) {
+        Acc buf[FB][K];
+#pragma unroll
+        for (int f = 0; f < FB; ++f)
+#pragma unroll
+            for (int q = 0; q < K; ++q) buf[f][q] = Acc::load_l2(part + ((base + (i + f) * stride) * C + l) * K + q);
+#pragma unroll
+        for (int f = 0; f < FB; ++f)
+#pragma unroll
+            for (int q = 0; q < K; ++q) tot[q].merge(buf[f][q]);
+    }
+    for (; i < count; ++i) {
+#pragma unroll
+        for (int q = 0; q < K; ++q) tot[q].merge(Acc::load_l2(part + ((base + i * stride) * C + l) * K + q));
+    }
+}
+
 // One thread of a long-row work unit.  Units are (long chunk lc, segment s)
 // pairs, numbered chunk by chunk (lunit[u] = {lc, s}); a unit has C threads,
 // virtual thread v = u*C + l takes lane l.  part holds K Accs per (unit,
-// lane); cnt one counter per (long chunk, lane), zero between products.
+// lane); cnt one counter per (long chunk, lane) and cnt2 one per (unit,
+// lane), all zero between products.
+//
+// Folding: a row of at most kSuper segments is folded in segment order by the
+// thread that completes its last segment.  A longer row folds in two levels:
+// each group of kSuper consecutive segments is folded in order by the thread
+// that completes the group (its result replaces the group's first partial),
+// then the thread that completes the last group folds the group results in
+// order.  Either way the result depends only on the row's entries.
 template <class VT, class XT, int K, int U, class Acc>
 __device__ __forceinline__ void long_unit(const VT *__restrict__ val, const int32_t *__restrict__ col,
                                           const int64_t *__restrict__ cs, const int32_t *__restrict__ srl,
                                           const int32_t *__restrict__ perm, const int32_t *__restrict__ lchunk,
-                                          const int2 *__restrict__ lunit, Acc *part, int32_t *cnt,
+                                          const int2 *__restrict__ lunit, Acc *part, int32_t *cnt, int32_t *cnt2,
                                           const XT *__restrict__ X, int64_t ldx, XT *Y, int64_t ldy,
                                           int64_t N, int C, int64_t v, int accumulate, bool vec,
                                           uint64_t pol) {
@@ -208,33 +244,30 @@ __device__ __forceinline__ void long_unit(const VT *__restrict__ val, const int3
                              pol);
 #pragma unroll
     for (int q = 0; q < K; ++q) part[(u * C + l) * K + q] = acc[q];
-    __threadfence();
-    int32_t *ct = cnt + (int64_t)us.x * C + l;
-    if (atomicAdd(ct, 1) != nseg - 1) return;
-    // this thread completed the row: fold the segments in order
-    __threadfence();
     const int64_t u0 = u - s;
+    int32_t *ct = cnt + (int64_t)us.x * C + l;
     Acc tot[K];
+    if (nseg <= kSuper) {
+        __threadfence();
+        if (atomicAdd(ct, 1) != nseg - 1) return;
+        __threadfence();  // this thread completed the row
+        fold_partials<K, Acc>(part, u0, 1, nseg, C, l, tot);
+    } else {
+        const int s0 = (s / kSuper) * kSuper;
+        const int ng = min(kSuper, nseg - s0);
+        int32_t *cg = cnt2 + (u0 + s0) * C + l;
+        __threadfence();
+        if (atomicAdd(cg, 1) != ng - 1) return;
+        __threadfence();  // this thread completed the group
+        fold_partials<K, Acc>(part, u0 + s0, 1, ng, C, l, tot);
+        *cg = 0;
 #pragma unroll
-    for (int q = 0; q < K; ++q) tot[q] = Acc::load_l2(part + (u0 * C + l) * K + q);
-    // the partials are loaded FB segments at a time (independent loads in
-    // flight) and folded in segment order
-    constexpr int FB = K >= 8 ? 2 : (K >= 4 ? 4 : 16 / K);
-    int s2 = 1;
-    for (; s2 + FB <= nseg; s2 += FB) {
-        Acc buf[FB][K];
-#pragma unroll
-        for (int f = 0; f < FB; ++f)
-#pragma unroll
-            for (int q = 0; q < K; ++q) buf[f][q] = Acc::load_l2(part + ((u0 + s2 + f) * C + l) * K + q);
-#pragma unroll
-        for (int f = 0; f < FB; ++f)
-#pragma unroll
-            for (int q = 0; q < K; ++q) tot[q].merge(buf[f][q]);
-    }
-    for (; s2 < nseg; ++s2) {
-#pragma unroll
-        for (int q = 0; q < K; ++q) tot[q].merge(Acc::load_l2(part + ((u0 + s2) * C + l) * K + q));
+        for (int q = 0; q < K; ++q) part[((u0 + s0) * C + l) * K + q] = tot[q];
+        __threadfence();
+        const int ngroups = (nseg + kSuper - 1) / kSuper;
+        if (atomicAdd(ct, 1) != ngroups - 1) return;
+        __threadfence();  // ... and the last group of the row
+        fold_partials<K, Acc>(part, u0, kSuper, ngroups, C, l, tot);
     }
 #pragma unroll
     for (int q = 0; q < K; ++q) Y[out * ldy + q] = tot[q].result();

@@ -24,6 +24,7 @@ __global__ void __launch_bounds__(512)
 k_spmmv(const VT *__restrict__ val, const int32_t *__restrict__ col, const int64_t *__restrict__ cs,
         const int32_t *__restrict__ srl, const int32_t *__restrict__ perm, const int32_t *__restrict__ lchunk,
         const int2 *__restrict__ lunit, int64_t long_threads, int64_t long_blocks, Acc *part, int32_t *cnt,
+        int32_t *cnt2,
         const typename XType<VT>::T *__restrict__ X, int64_t ldx, typename XType<VT>::T *Y, int64_t ldy,
         int64_t N, int C, int accumulate, int vec) {
     using XT = typename XType<VT>::T;
@@ -31,8 +32,8 @@ k_spmmv(const VT *__restrict__ val, const int32_t *__restrict__ col, const int64
     if (blockIdx.x < long_blocks) {
         const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
         if (v < long_threads)
-            long_unit<VT, XT, K, U, Acc>(val, col, cs, srl, perm, lchunk, lunit, part, cnt, X, ldx, Y, ldy, N, C,
-                                         v, accumulate, vec != 0, pol);
+            long_unit<VT, XT, K, U, Acc>(val, col, cs, srl, perm, lchunk, lunit, part, cnt, cnt2, X, ldx, Y, ldy,
+                                         N, C, v, accumulate, vec != 0, pol);
         return;
     }
     const int64_t r = (blockIdx.x - long_blocks) * (int64_t)blockDim.x + threadIdx.x;
@@ -50,7 +51,7 @@ cudaError_t run(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64
     k_spmmv<VT, K, U, Acc><<<(unsigned)grid, h->block, 0, s>>>(
         static_cast<const VT *>(h->val), h->col, h->cs, h->srl,
         (h->flags & SELL_BUILD_PERMUTE_COLS) ? nullptr : h->perm, h->lchunk, h->lunit, long_threads,
-        long_blocks, static_cast<Acc *>(h->part), h->cnt, static_cast<const XT *>(X), ldx,
+        long_blocks, static_cast<Acc *>(h->part), h->cnt, h->cnt2, static_cast<const XT *>(X), ldx,
         static_cast<XT *>(Y), ldy, h->nrows, h->C, acc, vec);
     return cudaGetLastError();
 }
@@ -58,7 +59,7 @@ cudaError_t run(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64
 // Same launch with caller-chosen segment scratch (used by sell_spmmv_noalloc).
 template <class VT, int K, int U, class Acc>
 cudaError_t run_with(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy, int acc,
-                     int vec, void *part, int32_t *cnt, cudaStream_t s) {
+                     int vec, void *part, int32_t *cnt, int32_t *cnt2, cudaStream_t s) {
     using XT = typename XType<VT>::T;
     const int64_t long_threads = h->nunits * h->C;
     const int64_t long_blocks = (long_threads + h->block - 1) / h->block;
@@ -66,19 +67,19 @@ cudaError_t run_with(const sell_matrix *h, const void *X, int64_t ldx, void *Y, 
     k_spmmv<VT, K, U, Acc><<<(unsigned)grid, h->block, 0, s>>>(
         static_cast<const VT *>(h->val), h->col, h->cs, h->srl,
         (h->flags & SELL_BUILD_PERMUTE_COLS) ? nullptr : h->perm, h->lchunk, h->lunit, long_threads,
-        long_blocks, static_cast<Acc *>(part), cnt, static_cast<const XT *>(X), ldx, static_cast<XT *>(Y),
+        long_blocks, static_cast<Acc *>(part), cnt, cnt2, static_cast<const XT *>(X), ldx, static_cast<XT *>(Y),
         ldy, h->nrows, h->C, acc, vec);
     return cudaGetLastError();
 }
 
 template <class VT, class Acc>
 cudaError_t pick_with(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy, int kb,
-                      int acc, int vec, void *part, int32_t *cnt, cudaStream_t s) {
+                      int acc, int vec, void *part, int32_t *cnt, int32_t *cnt2, cudaStream_t s) {
     switch (kb) {
-        case 1: return run_with<VT, 1, 4, Acc>(h, X, ldx, Y, ldy, acc, vec, part, cnt, s);
-        case 2: return run_with<VT, 2, 4, Acc>(h, X, ldx, Y, ldy, acc, vec, part, cnt, s);
-        case 4: return run_with<VT, 4, 2, Acc>(h, X, ldx, Y, ldy, acc, vec, part, cnt, s);
-        default: return run_with<VT, 8, 2, Acc>(h, X, ldx, Y, ldy, acc, vec, part, cnt, s);
+        case 1: return run_with<VT, 1, 4, Acc>(h, X, ldx, Y, ldy, acc, vec, part, cnt, cnt2, s);
+        case 2: return run_with<VT, 2, 4, Acc>(h, X, ldx, Y, ldy, acc, vec, part, cnt, cnt2, s);
+        case 4: return run_with<VT, 4, 2, Acc>(h, X, ldx, Y, ldy, acc, vec, part, cnt, cnt2, s);
+        default: return run_with<VT, 8, 2, Acc>(h, X, ldx, Y, ldy, acc, vec, part, cnt, cnt2, s);
     }
 }
 
@@ -165,7 +166,7 @@ sell_status launch_spmmv(sell_matrix *h, const void *X, int64_t ldx, void *Y, in
 // `part` (nunits * C * kb * 8 bytes) and zeroed counters `cnt` (nlong * C).
 sell_status launch_block_with_scratch(const sell_matrix *h, const void *X, int64_t ldx, void *Y,
                                       int64_t ldy, int kb, uint32_t flags, void *part, int32_t *cnt,
-                                      cudaStream_t s) {
+                                      int32_t *cnt2, cudaStream_t s) {
     const int acc = (flags & SELL_SPMV_ACCUMULATE) ? 1 : 0;
     const bool comp = (flags & SELL_SPMV_COMPENSATED) != 0;
     const size_t xs = h->store_type == SELL_F64 ? 8 : 4;
@@ -173,15 +174,15 @@ sell_status launch_block_with_scratch(const sell_matrix *h, const void *X, int64
     cudaError_t e;
     switch (h->store_type) {
         case SELL_F64:
-            e = pick_with<double, Plain<double>>(h, X, ldx, Y, ldy, kb, acc, vec, part, cnt, s);
+            e = pick_with<double, Plain<double>>(h, X, ldx, Y, ldy, kb, acc, vec, part, cnt, cnt2, s);
             break;
         case SELL_F32:
-            e = comp ? pick_with<float, Dot2>(h, X, ldx, Y, ldy, kb, acc, vec, part, cnt, s)
-                     : pick_with<float, Plain<float>>(h, X, ldx, Y, ldy, kb, acc, vec, part, cnt, s);
+            e = comp ? pick_with<float, Dot2>(h, X, ldx, Y, ldy, kb, acc, vec, part, cnt, cnt2, s)
+                     : pick_with<float, Plain<float>>(h, X, ldx, Y, ldy, kb, acc, vec, part, cnt, cnt2, s);
             break;
         default:
-            e = comp ? pick_with<__nv_bfloat16, Dot2>(h, X, ldx, Y, ldy, kb, acc, vec, part, cnt, s)
-                     : pick_with<__nv_bfloat16, Plain<float>>(h, X, ldx, Y, ldy, kb, acc, vec, part, cnt, s);
+            e = comp ? pick_with<__nv_bfloat16, Dot2>(h, X, ldx, Y, ldy, kb, acc, vec, part, cnt, cnt2, s)
+                     : pick_with<__nv_bfloat16, Plain<float>>(h, X, ldx, Y, ldy, kb, acc, vec, part, cnt, cnt2, s);
             break;
     }
     if (e != cudaSuccess) return cuda_fail(e, "SpMV kernel launch");

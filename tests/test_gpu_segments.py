@@ -3,7 +3,8 @@
 A row of length L <= 64 is one FMA chain in CRS order from y0 (0, or the old
 y when accumulating); a longer row is cut into segments of 64 entries, each an
 FMA chain (segment 0 from y0, the others from 0), and the segment results are
-added in order.  Here every FMA and every addition is emulated exactly with
+added in order -- for more than 64 segments first within each group of 64
+consecutive segments, then the group results in order.  Here every FMA and every addition is emulated exactly with
 rational arithmetic and one correct rounding to binary64 (float(Fraction) is
 correctly rounded), so the GPU result must match to the last bit."""
 from fractions import Fraction
@@ -15,6 +16,7 @@ from paper_1307_6209_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 SEG = 64
+SUPER = 64
 
 
 def _rnd(q: Fraction) -> float:
@@ -33,16 +35,23 @@ def _row_result(vals, xs, y0):
     if L <= SEG:
         return _chain(vals, xs, y0)
     parts = [_chain(vals[s:s + SEG], xs[s:s + SEG], y0 if s == 0 else 0.0) for s in range(0, L, SEG)]
-    t = parts[0]
-    for p in parts[1:]:
-        t = _rnd(Fraction(t) + Fraction(p))
-    return t
+
+    def fold(ps):
+        t = ps[0]
+        for p in ps[1:]:
+            t = _rnd(Fraction(t) + Fraction(p))
+        return t
+    if len(parts) <= SUPER:
+        return fold(parts)
+    # more than 64 segments: fold each group of 64 in order, then the groups
+    return fold([fold(parts[g:g + SUPER]) for g in range(0, len(parts), SUPER)])
 
 
 def _matrix():
-    lens = [0, 1, 5, 63, 64, 65, 100, 127, 128, 129, 192, 200, 257, 640, 1000, 3, 1500, 2000, 1089]
+    lens = [0, 1, 5, 63, 64, 65, 100, 127, 128, 129, 192, 200, 257, 640, 1000, 3, 1500, 2000, 1089, 4096,
+            4097, 4100, 9000]
     rng = np.random.default_rng(42)
-    n = 2048
+    n = 10000
     rows = []
     for i in range(300):
         L = lens[i % len(lens)] if i < 64 else int(rng.integers(0, 40))
