@@ -60,8 +60,8 @@ struct DevBuf {
 // the rounding of long rows.
 constexpr int kSeg = 64;
 // Segments per group of the two-level fold of very long rows (more than
-// kSeg * kSuper entries); also part of the numerics.
-constexpr int kSuper = 64;
+// kSeg * kSuper = 16384 entries); also part of the numerics.
+constexpr int kSuper = 256;
 
 inline size_t value_size(int t) { return t == SELL_F64 ? 8 : (t == SELL_F32 ? 4 : 2); }
 

@@ -11,8 +11,8 @@
 //               segment 0 is a chain starting at y0, every other segment a
 //               chain starting at 0; the segment results are then added in
 //               segment order (Dot2: merged with TwoSum, errors carried) --
-//               for more than kSuper segments, first within each group of
-//               kSuper consecutive segments, then the group results in order.
+//               for more than kSuper (256) segments, first within each group
+//               of kSuper consecutive segments, then the group results in order.
 // Every segment of a long row is an independent work unit, so long rows are
 // spread over the whole grid instead of holding one warp for their full
 // length (Sec. 3.4 notes that one thread per row leaves a warp waiting for

@@ -3,7 +3,7 @@
 A row of length L <= 64 is one FMA chain in CRS order from y0 (0, or the old
 y when accumulating); a longer row is cut into segments of 64 entries, each an
 FMA chain (segment 0 from y0, the others from 0), and the segment results are
-added in order -- for more than 64 segments first within each group of 64
+added in order -- for more than 256 segments first within each group of 256
 consecutive segments, then the group results in order.  Here every FMA and every addition is emulated exactly with
 rational arithmetic and one correct rounding to binary64 (float(Fraction) is
 correctly rounded), so the GPU result must match to the last bit."""
@@ -16,7 +16,7 @@ from paper_1307_6209_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 SEG = 64
-SUPER = 64
+SUPER = 256
 
 
 def _rnd(q: Fraction) -> float:
@@ -43,15 +43,15 @@ def _row_result(vals, xs, y0):
         return t
     if len(parts) <= SUPER:
         return fold(parts)
-    # more than 64 segments: fold each group of 64 in order, then the groups
+    # more than 256 segments: fold each group of 256 in order, then the groups
     return fold([fold(parts[g:g + SUPER]) for g in range(0, len(parts), SUPER)])
 
 
 def _matrix():
     lens = [0, 1, 5, 63, 64, 65, 100, 127, 128, 129, 192, 200, 257, 640, 1000, 3, 1500, 2000, 1089, 4096,
-            4097, 4100, 9000]
+            4100, 9000, 16384, 16385, 20000, 33000]
     rng = np.random.default_rng(42)
-    n = 10000
+    n = 40000
     rows = []
     for i in range(300):
         L = lens[i % len(lens)] if i < 64 else int(rng.integers(0, 40))
