@@ -167,25 +167,4 @@ __device__ __forceinline__ __nv_bfloat16 ld_stream(const __nv_bfloat16 *ptr, uin
     return __ushort_as_bfloat16(v);
 }
 
-// Gather of one right-hand-side element: the L2 line is kept with evict-last
-// priority against the streamed matrix (L1 allocation is kept: a small or
-// banded x is reused from L1).
-__device__ __forceinline__ uint64_t l2_evict_last_policy() {
-    uint64_t p;
-    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-__device__ __forceinline__ double ld_gather(const double *ptr) {
-    double v;
-    asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;"
-        : "=d"(v) : "l"(ptr), "l"(l2_evict_last_policy()));
-    return v;
-}
-__device__ __forceinline__ float ld_gather(const float *ptr) {
-    float v;
-    asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;"
-        : "=f"(v) : "l"(ptr), "l"(l2_evict_last_policy()));
-    return v;
-}
-
 }  // namespace sell

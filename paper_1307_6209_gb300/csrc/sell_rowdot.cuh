@@ -91,7 +91,7 @@ __device__ __forceinline__ void load_x(const XT *__restrict__ X, int64_t ldx, in
                                        XT (&xv)[K]) {
     const XT *p = X + (int64_t)ci * ldx;
     if constexpr (K == 1) {
-        xv[0] = ld_gather(p);
+        xv[0] = __ldg(p);
     } else {
         constexpr int V = 16 / sizeof(XT);  // elements per 16-byte vector
         if ((K % V) == 0 && vec) {
