@@ -318,7 +318,7 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ our arm
-def tune_launch(sell, h, xd, yd, stream, flags=0, blocks=(128, 256), unrolls=(1, 2, 4)):
+def tune_launch(sell, h, xd, yd, stream, flags=0, blocks=(128, 256), unrolls=(1, 2, 4, 8)):
     """Pick (block, unroll) for one handle by timing; returns (block, unroll, seconds)."""
     best = None
     for b in blocks:
