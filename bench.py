@@ -38,8 +38,8 @@ if ROOT not in sys.path:
 
 L2_BYTES = 129 * 2 ** 20
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SOURCES = ["paper_1307_6209_gb300/csrc/sell_spmv.cu", "paper_1307_6209_gb300/csrc/sell_internal.cuh",
-                  "paper_1307_6209_gb300/csrc/sell_rowdot.cuh"]
+KERNEL_SOURCES = ["paper_1307_6209_gb300/csrc/sell_spmv_impl.cuh", "paper_1307_6209_gb300/csrc/sell_spmv_f64.cu",
+                  "paper_1307_6209_gb300/csrc/sell_internal.cuh", "paper_1307_6209_gb300/csrc/sell_rowdot.cuh"]
 
 
 def parse_args():

@@ -1,0 +1,14 @@
+// sell_spmv_f32.cu -- SpMV / SpMMV kernels for float storage (instantiations
+// of sell_spmv_impl.cuh, kept in their own translation unit to compile in
+// parallel).
+#include "sell_spmv_impl.cuh"
+
+namespace sell {
+
+cudaError_t spmv_block_f32(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy, int kb,
+                           int acc, int vec, bool comp, void *part, int32_t *cnt, int32_t *cnt2, cudaStream_t s) {
+    return comp ? spmv_block<float, Dot2>(h, X, ldx, Y, ldy, kb, acc, vec, part, cnt, cnt2, s)
+                : spmv_block<float, Plain<float>>(h, X, ldx, Y, ldy, kb, acc, vec, part, cnt, cnt2, s);
+}
+
+}  // namespace sell
