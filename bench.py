@@ -319,16 +319,17 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ our arm
 def tune_launch(sell, h, xd, yd, stream, flags=0, blocks=(128, 256), unrolls=(1, 2, 4, 8)):
-    """Pick (block, unroll) for one handle by timing; returns (block, unroll, seconds)."""
-    best = None
-    for b in blocks:
-        for u in unrolls:
+    """Pick (block, unroll) for one handle: two interleaved timing rounds of
+    every candidate, best of the two; returns (block, unroll, seconds)."""
+    cands = [(b, u) for b in blocks for u in unrolls]
+    best_t = {c: 1e30 for c in cands}
+    for _ in range(2):
+        for b, u in cands:
             sell.sell_set_launch(h, b, u)
-            dt = time_spmv(sell, h, xd, yd, stream, reps=30, flags=flags)
-            if best is None or dt < best[2]:
-                best = (b, u, dt)
-    sell.sell_set_launch(h, best[0], best[1])
-    return best
+            best_t[(b, u)] = min(best_t[(b, u)], time_spmv(sell, h, xd, yd, stream, reps=50, flags=flags))
+    (b, u), t = min(best_t.items(), key=lambda kv: kv[1])
+    sell.sell_set_launch(h, b, u)
+    return b, u, t
 
 
 def stencil_section(sell, model, stream, peak, fma_tf, n=200):
