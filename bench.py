@@ -318,18 +318,19 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ our arm
-def tune_launch(sell, h, xd, yd, stream, flags=0, blocks=(128, 256), unrolls=(1, 2, 4, 8)):
-    """Pick (block, unroll) for one handle: two interleaved timing rounds of
-    every candidate, best of the two; returns (block, unroll, seconds)."""
-    cands = [(b, u) for b in blocks for u in unrolls]
+def tune_launch(sell, h, xd, yd, stream, flags=0, blocks=(128, 256), unrolls=(1, 2, 4, 8), pipelines=(0, 1)):
+    """Pick (block, unroll, pipeline) for one handle: two interleaved timing
+    rounds of every candidate, best of the two; returns (block, unroll,
+    pipeline, seconds)."""
+    cands = [(b, u, p) for b in blocks for u in unrolls for p in pipelines]
     best_t = {c: 1e30 for c in cands}
     for _ in range(2):
-        for b, u in cands:
-            sell.sell_set_launch(h, b, u)
-            best_t[(b, u)] = min(best_t[(b, u)], time_spmv(sell, h, xd, yd, stream, reps=50, flags=flags))
-    (b, u), t = min(best_t.items(), key=lambda kv: kv[1])
-    sell.sell_set_launch(h, b, u)
-    return b, u, t
+        for c in cands:
+            sell.sell_set_launch(h, *c)
+            best_t[c] = min(best_t[c], time_spmv(sell, h, xd, yd, stream, reps=50, flags=flags))
+    c, t = min(best_t.items(), key=lambda kv: kv[1])
+    sell.sell_set_launch(h, *c)
+    return c[0], c[1], c[2], t
 
 
 def stencil_section(sell, model, stream, peak, fma_tf, n=200):
@@ -347,7 +348,7 @@ def stencil_section(sell, model, stream, peak, fma_tf, n=200):
         bms = (time.perf_counter() - t0) * 1e3
         xs = x if st == sell.SELL_F64 else x.float()
         ys = torch.empty(A.nrows, dtype=xs.dtype, device="cuda")
-        blk, unr, _ = tune_launch(sell, h, xs, ys, stream)
+        blk, unr, pip, _ = tune_launch(sell, h, xs, ys, stream)
         dt = time_spmv(sell, h, xs, ys, stream, reps=200)
         torch.cuda.synchronize()
         vb = 8 if st == sell.SELL_F64 else (4 if st == sell.SELL_F32 else 2)
@@ -355,7 +356,8 @@ def stencil_section(sell, model, stream, peak, fma_tf, n=200):
         alg = model.algorithmic_bytes(A.nrows, A.ncols, A.nnz, h.info.nchunks, 32, vb, xb, False)
         row = {"us": round(dt * 1e6, 2), "gflops": round(2.0 * A.nnz / dt / 1e9, 1),
                "gbs": round(alg / dt / 1e9, 1), "hbm_frac": round(alg / dt / 1e9 / peak, 4),
-               "block": blk, "unroll": unr, "build_ms": round(bms, 1), "beta": round(h.info.beta, 6)}
+               "block": blk, "unroll": unr, "pipeline": pip, "build_ms": round(bms, 1),
+               "beta": round(h.info.beta, 6)}
         if st == sell.SELL_F64:
             y64 = ys.clone()
             if fma_tf:
@@ -561,13 +563,13 @@ def pathological_section(sell, model, stream, peak):
         y = torch.empty(A.nrows, dtype=torch.float64, device="cuda")
         for C, sg in fmts:
             h = sell.sell_build(A, C=C, sigma=sg, stream=stream)
-            blk, unr, _ = tune_launch(sell, h, x, y, stream)
+            blk, unr, pip, _ = tune_launch(sell, h, x, y, stream)
             dt = time_spmv(sell, h, x, y, stream, reps=50)
             alg = model.algorithmic_bytes(A.nrows, A.ncols, A.nnz, h.info.nchunks, C, 8, 8, h.info.has_perm)
             out[f"{name}_C{C}_s{sg}"] = {"nnz": A.nnz, "us": round(dt * 1e6, 2),
                                           "gflops": round(2.0 * A.nnz / dt / 1e9, 1),
                                           "hbm_frac": round(alg / dt / 1e9 / peak, 4), "beta": round(h.info.beta, 4),
-                                          "block": blk, "unroll": unr}
+                                          "block": blk, "unroll": unr, "pipeline": pip}
             h.free()
         del A, x, y
         torch.cuda.empty_cache()
@@ -696,12 +698,13 @@ def run_ours(args):
                 y32 = torch.empty(A.nrows, dtype=torch.float32, device="cuda")
                 row = {}
                 for tag, fl in (("plain", 0), ("dot2", sell.SELL_SPMV_COMPENSATED)):
-                    blk, unr, _ = tune_launch(sell, hm, x32, y32, stream, flags=fl)
+                    blk, unr, pip, _ = tune_launch(sell, hm, x32, y32, stream, flags=fl)
                     dt = time_spmv(sell, hm, x32, y32, stream, reps=100, flags=fl)
                     torch.cuda.synchronize()
                     err = (y32.double() - y64).abs()
                     row[tag] = {"gflops": round(flops / dt / 1e9, 1), "us": round(dt * 1e6, 2),
                                 "speedup_vs_f64": round(kern_s / dt, 3), "block": blk, "unroll": unr,
+                                "pipeline": pip,
                                 "max_abs_err_vs_f64": float(err.max()),
                                 "rel_err_vs_f64": float(err.norm() / y64.norm())}
                 mixed[name] = row
@@ -723,7 +726,8 @@ def run_ours(args):
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": traffic,
             "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
-            "kernel": f"k_spmmv<double,1,{best.unroll},Plain<double>> block {best.block}",
+            "kernel": (f"k_spmmv<double,1,{best.unroll},{'true' if best.pipeline else 'false'},Plain<double>> "
+                       f"block {best.block}"),
             "kernel_avg_us": round(kern_s * 1e6, 3), "algorithmic_bytes_per_launch": alg}
     nnzr = A.nnz / A.nrows
     bal = model.balance_sell(1.0 / nnzr, inf.beta, nnzr)
@@ -743,7 +747,8 @@ def run_ours(args):
     extras["fp64_fma_peak_tflops"] = round(fma_tf, 3)
     extras["fp64_pipe_frac"] = round(flops / kern_s / 1e12 / fma_tf, 4)
     extras["build_ms"] = round(build_ms, 2)
-    extras["tuned"] = {"C": C, "sigma": sigma, "block": best.block, "unroll": best.unroll}
+    extras["tuned"] = {"C": C, "sigma": sigma, "block": best.block, "unroll": best.unroll,
+                       "pipeline": best.pipeline}
     extras["sweep"] = sweep
     extras["device"] = dev_name
 

@@ -196,9 +196,12 @@ SELL_API sell_status sell_spmmv_noalloc(sell_handle h, const void *X, int64_t ld
                                         int32_t k, uint32_t flags, void *stream);
 
 /* Launch tuning of a handle's SpMV/SpMMV kernels (autotuner knob):
- * block = threads per block (32..512, multiple of 32), unroll = independent
- * loads in flight per thread (1, 2, 4 or 8).  0 keeps the current value. */
-SELL_API sell_status sell_set_launch(sell_handle h, int32_t block, int32_t unroll);
+ * block = threads per block (32..512, multiple of 32), unroll = entries of a
+ * row loaded per step (1, 2, 4 or 8), pipeline = 1 issues the next step's
+ * matrix loads before the current step's gathers (software pipelining, for
+ * 1 and 2 right-hand sides), 0 does not.  block or unroll 0 and pipeline -1
+ * keep the current value.  The results do not depend on any of them. */
+SELL_API sell_status sell_set_launch(sell_handle h, int32_t block, int32_t unroll, int32_t pipeline);
 
 /* Fill *info (host struct).  Errors: SELL_EINVAL. */
 SELL_API sell_status sell_info(sell_handle h, sell_info_t *info);

@@ -1,10 +1,11 @@
-"""Autotuner for SELL-C-sigma on GB300: picks C, sigma, the block size and the
-unroll depth of the SpMV by measurement.
+"""Autotuner for SELL-C-sigma on GB300: picks C, sigma, the block size, the
+unroll depth and the software pipelining of the SpMV by measurement.
 
 The paper leaves the choice of sigma and of the threads per row to future
 work (Sec. 6) and notes that the best sigma is matrix dependent (Sec. 3.4,
 Sec. 5.3).  Stage 1 builds every (C, sigma) candidate and times the SpMV with
-the default launch; stage 2 sweeps (block, unroll) on the best formats.  All
+the default launch; stage 2 sweeps (block, unroll, pipeline) on the best
+formats (pipeline only for 1 and 2 right-hand sides, where it exists).  All
 timing goes through the C ABI (CUDA events on the given stream).  Results are
 cached in a JSON file keyed by a matrix signature (sizes, longest row, the
 coefficient of variation of Eq. "cv", storage type, right-hand sides).
@@ -30,13 +31,14 @@ class Choice:
     unroll: int
     us: float
     gflops: float
+    pipeline: int = 0
 
 
 @dataclass
 class TuneResult:
     best: Choice
     formats: list = field(default_factory=list)  # stage 1: (C, sigma, beta, us, build_ms)
-    launches: list = field(default_factory=list)  # stage 2: (C, sigma, block, unroll, us)
+    launches: list = field(default_factory=list)  # stage 2: (C, sigma, block, unroll, pipeline, us)
     cached: bool = False
 
 
@@ -78,10 +80,11 @@ def _save_cache(path, data):
 
 
 def tune(A, store_type: int = sell.SELL_F64, k: int = 1, Cs=(32, 64, 128), sigmas=None,
-         blocks=(128, 256, 512), unrolls=(1, 2, 4, 8), keep: int = 2, reps: int = 30, stream=None,
+         blocks=(128, 256, 512), unrolls=(1, 2, 4, 8), pipelines=(0, 1), keep: int = 2, reps: int = 30,
+         stream=None,
          cache: str | None = DEFAULT_CACHE, use_cache: bool = True) -> TuneResult:
     """Tune the SpMV (k = 1) or SpMMV (k > 1) of CSR matrix A (host numpy or
-    device torch arrays).  Returns the best (C, sigma, block, unroll)."""
+    device torch arrays).  Returns the best (C, sigma, block, unroll, pipeline)."""
     import torch
 
     stream = stream or torch.cuda.current_stream()
@@ -124,11 +127,13 @@ def tune(A, store_type: int = sell.SELL_F64, k: int = 1, Cs=(32, 64, 128), sigma
         h = built[(r["C"], r["sigma"])]
         for b in blocks:
             for u in unrolls:
-                sell.sell_set_launch(h, b, u)
-                us = _time(lambda: product(h), stream, reps)
-                launches.append({"C": r["C"], "sigma": r["sigma"], "block": b, "unroll": u, "us": us})
-                if best is None or us < best.us:
-                    best = Choice(r["C"], r["sigma"], b, u, us, flops / us / 1e3)
+                for p in (pipelines if k <= 2 else (0,)):
+                    sell.sell_set_launch(h, b, u, p)
+                    us = _time(lambda: product(h), stream, reps)
+                    launches.append({"C": r["C"], "sigma": r["sigma"], "block": b, "unroll": u, "pipeline": p,
+                                     "us": us})
+                    if best is None or us < best.us:
+                        best = Choice(r["C"], r["sigma"], b, u, us, flops / us / 1e3, p)
     for h in built.values():
         h.free()
     if cache:
@@ -141,7 +146,7 @@ def tune(A, store_type: int = sell.SELL_F64, k: int = 1, Cs=(32, 64, 128), sigma
 def build_tuned(A, choice: Choice, store_type: int = sell.SELL_F64, stream=None) -> "sell.SellMatrix":
     """Build the handle the tuner chose and apply its launch shape."""
     h = sell.sell_build(A, C=choice.C, sigma=choice.sigma, store_type=store_type, stream=stream)
-    sell.sell_set_launch(h, choice.block, choice.unroll)
+    sell.sell_set_launch(h, choice.block, choice.unroll, choice.pipeline)
     return h
 
 

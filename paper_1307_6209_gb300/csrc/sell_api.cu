@@ -163,14 +163,16 @@ sell_status sell_spmv(sell_handle h, const void *x, void *y, uint32_t flags, voi
     return sell_spmmv(h, x, 1, y, 1, 1, flags, stream);
 }
 
-sell_status sell_set_launch(sell_handle h, int32_t block, int32_t unroll) {
+sell_status sell_set_launch(sell_handle h, int32_t block, int32_t unroll, int32_t pipeline) {
     if (!h) return fail(SELL_EINVAL, "sell_set_launch: NULL handle");
     if (block != 0 && (block < 32 || block > 512 || block % 32 != 0))
         return fail(SELL_EINVAL, "sell_set_launch: block must be a multiple of 32 in [32, 512]");
     if (unroll != 0 && unroll != 1 && unroll != 2 && unroll != 4 && unroll != 8)
         return fail(SELL_EINVAL, "sell_set_launch: unroll must be 1, 2, 4 or 8");
+    if (pipeline < -1 || pipeline > 1) return fail(SELL_EINVAL, "sell_set_launch: pipeline must be -1, 0 or 1");
     if (block) h->block = block;
     if (unroll) h->unroll = unroll;
+    if (pipeline >= 0) h->pipeline = pipeline;
     return SELL_OK;
 }
 

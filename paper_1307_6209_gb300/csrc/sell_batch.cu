@@ -79,7 +79,7 @@ k_batch(const __grid_constant__ LaunchParams lp) {
     if (u.kind == 1) {
         const int64_t v = u.idx + threadIdx.x;
         if (v < P.long_threads)
-            long_unit<VT, XT, K, U, Acc>(static_cast<const VT *>(P.val), P.col, P.cs, P.srl, P.perm, P.lchunk,
+            long_unit<VT, XT, K, U, false, Acc>(static_cast<const VT *>(P.val), P.col, P.cs, P.srl, P.perm, P.lchunk,
                                          P.lunit, static_cast<Acc *>(P.part), P.cnt, P.cnt2,
                                          static_cast<const XT *>(P.X),
                                          P.ldx, static_cast<XT *>(P.Y), P.ldy, P.N, P.C, v, P.acc, P.vec != 0, pol);
@@ -87,7 +87,7 @@ k_batch(const __grid_constant__ LaunchParams lp) {
     }
     const int64_t r = u.idx + threadIdx.x;
     if (r < P.N)
-        short_row<VT, XT, K, U, Acc>(static_cast<const VT *>(P.val), P.col, P.cs, P.srl, P.perm,
+        short_row<VT, XT, K, U, false, Acc>(static_cast<const VT *>(P.val), P.col, P.cs, P.srl, P.perm,
                                      static_cast<const XT *>(P.X), P.ldx, static_cast<XT *>(P.Y), P.ldy, P.C, r, P.acc,
                                      P.vec != 0, pol);
 }

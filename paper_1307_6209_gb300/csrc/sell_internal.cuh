@@ -74,7 +74,7 @@ struct sell_matrix {
     uint32_t flags = 0;
     double beta = 1.0, zeta = 0.0;
     int device = 0;
-    int32_t block = 256, unroll = 4;
+    int32_t block = 256, unroll = 4, pipeline = 0;
     sell::Allocator al;
     // device arrays (owned)
     void *val = nullptr;       // stored elements of store_type

@@ -122,8 +122,11 @@ __device__ __forceinline__ void load_x(const XT *__restrict__ X, int64_t ldx, in
 // One chain over entries j0..j1-1 of a row whose entry j sits at vp[j*C]
 // (values) and cp[j*C] (columns), in entry order.  Full groups of U entries
 // are loaded before their gathers and FMAs; the last, partial group is loaded
-// with predicates so that short rows keep all their loads in flight.
-template <class VT, class XT, int K, int U, class Acc>
+// with predicates so that short rows keep all their loads in flight.  With
+// PIPE the stream loads of the next group are issued before the gathers and
+// FMAs of the current one (software pipelining: more bytes in flight per
+// thread; the order of the FMAs is unchanged).
+template <class VT, class XT, int K, int U, bool PIPE, class Acc>
 __device__ __forceinline__ void chain(Acc (&acc)[K], const VT *__restrict__ vp,
                                       const int32_t *__restrict__ cp, int C, int j0, int j1,
                                       const XT *__restrict__ X, int64_t ldx, bool vec, uint64_t pol) {
@@ -131,25 +134,67 @@ __device__ __forceinline__ void chain(Acc (&acc)[K], const VT *__restrict__ vp,
     vp += (int64_t)j0 * stride;
     cp += (int64_t)j0 * stride;
     int j = j0;
-    for (; j + U <= j1; j += U) {
-        VT v[U];
-        int32_t ci[U];
+    if constexpr (PIPE) {
+        if (j + U <= j1) {
+            VT v[U];
+            int32_t ci[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            v[u] = ld_stream(vp + u * stride, pol);
-            ci[u] = ld_stream(cp + u * stride, pol);
+            for (int u = 0; u < U; ++u) {
+                v[u] = ld_stream(vp + u * stride, pol);
+                ci[u] = ld_stream(cp + u * stride, pol);
+            }
+            for (;;) {
+                const bool more = j + 2 * U <= j1;
+                VT vn[U];
+                int32_t cn[U];
+                if (more) {
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        vn[u] = ld_stream(vp + (U + u) * stride, pol);
+                        cn[u] = ld_stream(cp + (U + u) * stride, pol);
+                    }
+                }
+                XT xv[U][K];
+#pragma unroll
+                for (int u = 0; u < U; ++u) load_x<K>(X, ldx, ci[u], vec, xv[u]);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    XT a = widen(v[u]);
+#pragma unroll
+                    for (int q = 0; q < K; ++q) acc[q].add(a, xv[u][q]);
+                }
+                vp += U * stride;
+                cp += U * stride;
+                j += U;
+                if (!more) break;
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    v[u] = vn[u];
+                    ci[u] = cn[u];
+                }
+            }
         }
-        XT xv[U][K];
+    } else {
+        for (; j + U <= j1; j += U) {
+            VT v[U];
+            int32_t ci[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) load_x<K>(X, ldx, ci[u], vec, xv[u]);
+            for (int u = 0; u < U; ++u) {
+                v[u] = ld_stream(vp + u * stride, pol);
+                ci[u] = ld_stream(cp + u * stride, pol);
+            }
+            XT xv[U][K];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            XT a = widen(v[u]);
+            for (int u = 0; u < U; ++u) load_x<K>(X, ldx, ci[u], vec, xv[u]);
 #pragma unroll
-            for (int q = 0; q < K; ++q) acc[q].add(a, xv[u][q]);
+            for (int u = 0; u < U; ++u) {
+                XT a = widen(v[u]);
+#pragma unroll
+                for (int q = 0; q < K; ++q) acc[q].add(a, xv[u][q]);
+            }
+            vp += U * stride;
+            cp += U * stride;
         }
-        vp += U * stride;
-        cp += U * stride;
     }
     if constexpr (U > 1) {
         if (j < j1) {
@@ -216,7 +261,7 @@ __device__ __forceinline__ void fold_partials(const Acc *part, int64_t base, int
 // that completes the group (its result replaces the group's first partial),
 // then the thread that completes the last group folds the group results in
 // order.  Either way the result depends only on the row's entries.
-template <class VT, class XT, int K, int U, class Acc>
+template <class VT, class XT, int K, int U, bool PIPE, class Acc>
 __device__ __forceinline__ void long_unit(const VT *__restrict__ val, const int32_t *__restrict__ col,
                                           const int64_t *__restrict__ cs, const int32_t *__restrict__ srl,
                                           const int32_t *__restrict__ perm, const int32_t *__restrict__ lchunk,
@@ -240,8 +285,8 @@ __device__ __forceinline__ void long_unit(const VT *__restrict__ val, const int3
 #pragma unroll
     for (int q = 0; q < K; ++q) acc[q].init((s == 0 && accumulate) ? Y[out * ldy + q] : XT(0));
     const int64_t base = cs[c] + l;
-    chain<VT, XT, K, U, Acc>(acc, val + base, col + base, C, s * kSeg, min(L, (s + 1) * kSeg), X, ldx, vec,
-                             pol);
+    chain<VT, XT, K, U, PIPE, Acc>(acc, val + base, col + base, C, s * kSeg, min(L, (s + 1) * kSeg), X, ldx,
+                                   vec, pol);
 #pragma unroll
     for (int q = 0; q < K; ++q) part[(u * C + l) * K + q] = acc[q];
     const int64_t u0 = u - s;
@@ -275,7 +320,7 @@ __device__ __forceinline__ void long_unit(const VT *__restrict__ val, const int3
 }
 
 // The thread's own row when it is short (L <= kSeg); long rows return.
-template <class VT, class XT, int K, int U, class Acc>
+template <class VT, class XT, int K, int U, bool PIPE, class Acc>
 __device__ __forceinline__ void short_row(const VT *__restrict__ val, const int32_t *__restrict__ col,
                                           const int64_t *__restrict__ cs, const int32_t *__restrict__ srl,
                                           const int32_t *__restrict__ perm, const XT *__restrict__ X,
@@ -290,7 +335,7 @@ __device__ __forceinline__ void short_row(const VT *__restrict__ val, const int3
     Acc acc[K];
 #pragma unroll
     for (int q = 0; q < K; ++q) acc[q].init(accumulate ? Y[out * ldy + q] : XT(0));
-    chain<VT, XT, K, U, Acc>(acc, val + base, col + base, C, 0, L, X, ldx, vec, pol);
+    chain<VT, XT, K, U, PIPE, Acc>(acc, val + base, col + base, C, 0, L, X, ldx, vec, pol);
 #pragma unroll
     for (int q = 0; q < K; ++q) Y[out * ldy + q] = acc[q].result();
 }

@@ -26,7 +26,7 @@ namespace sell {
 namespace spmv_impl {
 
 
-template <class VT, int K, int U, class Acc, bool LONG>
+template <class VT, int K, int U, bool PIPE, class Acc, bool LONG>
 __global__ void __launch_bounds__(512)
 k_spmmv(const VT *__restrict__ val, const int32_t *__restrict__ col, const int64_t *__restrict__ cs,
         const int32_t *__restrict__ srl, const int32_t *__restrict__ perm, const int32_t *__restrict__ lchunk,
@@ -40,17 +40,17 @@ k_spmmv(const VT *__restrict__ val, const int32_t *__restrict__ col, const int64
         if (blockIdx.x < long_blocks) {
             const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
             if (v < long_threads)
-                long_unit<VT, XT, K, U, Acc>(val, col, cs, srl, perm, lchunk, lunit, part, cnt, cnt2, X, ldx, Y,
+                long_unit<VT, XT, K, U, PIPE, Acc>(val, col, cs, srl, perm, lchunk, lunit, part, cnt, cnt2, X, ldx, Y,
                                              ldy, N, C, v, accumulate, vec != 0, pol);
             return;
         }
     }
     const int64_t r = (blockIdx.x - long_blocks) * (int64_t)blockDim.x + threadIdx.x;
     if (r >= N) return;
-    short_row<VT, XT, K, U, Acc>(val, col, cs, srl, perm, X, ldx, Y, ldy, C, r, accumulate, vec != 0, pol);
+    short_row<VT, XT, K, U, PIPE, Acc>(val, col, cs, srl, perm, X, ldx, Y, ldy, C, r, accumulate, vec != 0, pol);
 }
 
-template <class VT, int K, int U, class Acc>
+template <class VT, int K, int U, bool PIPE, class Acc>
 cudaError_t run(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy, int acc,
                 int vec, cudaStream_t s) {
     using XT = typename XType<VT>::T;
@@ -59,7 +59,7 @@ cudaError_t run(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64
     const int64_t grid = long_blocks + (h->nrows + h->block - 1) / h->block;
     // without long rows the long-row path is compiled out, so that it does
     // not cost the per-row path registers or scheduling freedom
-    auto kern = h->nunits ? k_spmmv<VT, K, U, Acc, true> : k_spmmv<VT, K, U, Acc, false>;
+    auto kern = h->nunits ? k_spmmv<VT, K, U, PIPE, Acc, true> : k_spmmv<VT, K, U, PIPE, Acc, false>;
     kern<<<(unsigned)grid, h->block, 0, s>>>(
         static_cast<const VT *>(h->val), h->col, h->cs, h->srl,
         (h->flags & SELL_BUILD_PERMUTE_COLS) ? nullptr : h->perm, h->lchunk, h->lunit, long_threads,
@@ -69,14 +69,14 @@ cudaError_t run(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64
 }
 
 // Same launch with caller-chosen segment scratch (used by sell_spmmv_noalloc).
-template <class VT, int K, int U, class Acc>
+template <class VT, int K, int U, bool PIPE, class Acc>
 cudaError_t run_with(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy, int acc,
                      int vec, void *part, int32_t *cnt, int32_t *cnt2, cudaStream_t s) {
     using XT = typename XType<VT>::T;
     const int64_t long_threads = h->nunits * h->C;
     const int64_t long_blocks = (long_threads + h->block - 1) / h->block;
     const int64_t grid = long_blocks + (h->nrows + h->block - 1) / h->block;
-    auto kern = h->nunits ? k_spmmv<VT, K, U, Acc, true> : k_spmmv<VT, K, U, Acc, false>;
+    auto kern = h->nunits ? k_spmmv<VT, K, U, PIPE, Acc, true> : k_spmmv<VT, K, U, PIPE, Acc, false>;
     kern<<<(unsigned)grid, h->block, 0, s>>>(
         static_cast<const VT *>(h->val), h->col, h->cs, h->srl,
         (h->flags & SELL_BUILD_PERMUTE_COLS) ? nullptr : h->perm, h->lchunk, h->lunit, long_threads,
@@ -89,31 +89,42 @@ template <class VT, class Acc>
 cudaError_t pick_with(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy, int kb,
                       int acc, int vec, void *part, int32_t *cnt, int32_t *cnt2, cudaStream_t s) {
     switch (kb) {
-        case 1: return run_with<VT, 1, 4, Acc>(h, X, ldx, Y, ldy, acc, vec, part, cnt, cnt2, s);
-        case 2: return run_with<VT, 2, 4, Acc>(h, X, ldx, Y, ldy, acc, vec, part, cnt, cnt2, s);
-        case 4: return run_with<VT, 4, 2, Acc>(h, X, ldx, Y, ldy, acc, vec, part, cnt, cnt2, s);
-        default: return run_with<VT, 8, 2, Acc>(h, X, ldx, Y, ldy, acc, vec, part, cnt, cnt2, s);
+        case 1: return run_with<VT, 1, 4, false, Acc>(h, X, ldx, Y, ldy, acc, vec, part, cnt, cnt2, s);
+        case 2: return run_with<VT, 2, 4, false, Acc>(h, X, ldx, Y, ldy, acc, vec, part, cnt, cnt2, s);
+        case 4: return run_with<VT, 4, 2, false, Acc>(h, X, ldx, Y, ldy, acc, vec, part, cnt, cnt2, s);
+        default: return run_with<VT, 8, 2, false, Acc>(h, X, ldx, Y, ldy, acc, vec, part, cnt, cnt2, s);
     }
 }
 
 // Unroll choices keep U * K <= 16 gathered values per thread.
+template <class VT, int K, bool PIPE, class Acc>
+cudaError_t pick_u(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy, int acc, int vec,
+                   cudaStream_t s) {
+    int u = h->unroll;
+    if constexpr (K >= 8) {
+        return u >= 2 ? run<VT, K, 2, PIPE, Acc>(h, X, ldx, Y, ldy, acc, vec, s)
+                      : run<VT, K, 1, PIPE, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
+    } else if constexpr (K >= 4) {
+        if (u >= 4) return run<VT, K, 4, PIPE, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
+        if (u >= 2) return run<VT, K, 2, PIPE, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
+        return run<VT, K, 1, PIPE, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
+    } else {
+        if (u >= 8) return run<VT, K, 8, PIPE, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
+        if (u >= 4) return run<VT, K, 4, PIPE, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
+        if (u >= 2) return run<VT, K, 2, PIPE, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
+        return run<VT, K, 1, PIPE, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
+    }
+}
+
+// The software-pipelined chain is built for 1 and 2 right-hand sides (wider
+// blocks already keep many loads in flight and would double their registers).
 template <class VT, int K, class Acc>
 cudaError_t pick_unroll(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy,
                         int acc, int vec, cudaStream_t s) {
-    int u = h->unroll;
-    if constexpr (K >= 8) {
-        return u >= 2 ? run<VT, K, 2, Acc>(h, X, ldx, Y, ldy, acc, vec, s)
-                      : run<VT, K, 1, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
-    } else if constexpr (K >= 4) {
-        if (u >= 4) return run<VT, K, 4, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
-        if (u >= 2) return run<VT, K, 2, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
-        return run<VT, K, 1, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
-    } else {
-        if (u >= 8) return run<VT, K, 8, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
-        if (u >= 4) return run<VT, K, 4, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
-        if (u >= 2) return run<VT, K, 2, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
-        return run<VT, K, 1, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
+    if constexpr (K <= 2) {
+        if (h->pipeline) return pick_u<VT, K, true, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
     }
+    return pick_u<VT, K, false, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
 }
 
 template <class VT, class Acc>
@@ -126,7 +137,6 @@ cudaError_t pick_k(const sell_matrix *h, const void *X, int64_t ldx, void *Y, in
         default: return pick_unroll<VT, 8, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
     }
 }
-
 
 }  // namespace spmv_impl
 

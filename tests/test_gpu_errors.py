@@ -57,6 +57,8 @@ def test_bad_options_are_einval():
     h = sell.sell_build(synth.laplace2d(8), C=32)
     assert _status(sell.sell_set_launch, h, 48, 0) == sell.SELL_EINVAL
     assert _status(sell.sell_set_launch, h, 0, 3) == sell.SELL_EINVAL
+    assert _status(sell.sell_set_launch, h, 0, 0, 2) == sell.SELL_EINVAL
+    assert _status(sell.sell_set_launch, h, 0, 0, -2) == sell.SELL_EINVAL
     lib = sell.load()
     assert lib.sell_spmmv(h.handle, None, 1, None, 1, 0, 0, None) == sell.SELL_EINVAL
     assert lib.sell_spmv(None, None, None, 0, None) == sell.SELL_EINVAL

@@ -23,9 +23,9 @@ def lognormal2m():
     return synth.lognormal(2_000_000, mean=16.0, sigma_ln=1.2, cap=2000, seed=0)
 
 
-@pytest.mark.parametrize("C,sigma,block,unroll", [(64, 2_000_000, 128, 4), (32, 2_000_000, 128, 8),
-                                                  (32, 1, 256, 4), (128, 4096, 128, 2)])
-def test_lognormal_2m_full(lognormal2m, C, sigma, block, unroll):
+@pytest.mark.parametrize("C,sigma,block,unroll,pipe", [(64, 2_000_000, 128, 4, 1), (32, 2_000_000, 128, 8, 0),
+                                                       (32, 1, 256, 4, 1), (128, 4096, 128, 2, 0)])
+def test_lognormal_2m_full(lognormal2m, C, sigma, block, unroll, pipe):
     import torch
     from paper_1307_6209_gb300 import sell
 
@@ -35,7 +35,7 @@ def test_lognormal_2m_full(lognormal2m, C, sigma, block, unroll):
     F = oracle.sell_build(A, C, sigma)
     for k in ("cs", "cl", "srl", "perm", "col", "val"):
         assert G[k].tobytes() == F[k].tobytes(), k
-    sell.sell_set_launch(h, block, unroll)
+    sell.sell_set_launch(h, block, unroll, pipe)
     x = synth.vector(A.ncols, seed=0)
     xd = torch.from_numpy(x).cuda()
     yd = torch.empty(A.nrows, dtype=torch.float64, device="cuda")
@@ -57,7 +57,7 @@ def test_stencil27_200_full():
     A = synth.CSR(Ad.nrows, Ad.ncols, Ad.rpt.cpu().numpy(), Ad.col.cpu().numpy(), Ad.val.cpu().numpy())
     assert A.nnz == (3 * n - 2) ** 3 == 213_847_192
     h = sell.sell_build(Ad, C=32, sigma=1)
-    sell.sell_set_launch(h, 128, 1)
+    sell.sell_set_launch(h, 128, 4, 1)
     x = synth.vector(A.ncols, seed=0)
     xd = torch.from_numpy(x).cuda()
     yd = torch.empty(A.nrows, dtype=torch.float64, device="cuda")
@@ -93,7 +93,7 @@ def test_stencil27_200_full():
 
     # binary32 storage at full size: within the binary32 FMA-chain bound
     h32 = sell.sell_build(Ad, C=32, sigma=1, store_type=sell.SELL_F32)
-    sell.sell_set_launch(h32, 128, 4)
+    sell.sell_set_launch(h32, 128, 8, 1)
     x32 = x.astype(np.float32)
     y32 = torch.empty(A.nrows, dtype=torch.float32, device="cuda")
     sell.sell_spmv(h32, torch.from_numpy(x32).cuda(), y32)

@@ -63,7 +63,8 @@ def test_compensated_on_f64_is_unsupported():
 
 
 def test_mixed_invariant_across_formats():
-    """The binary32 chain is also bitwise independent of (C, sigma)."""
+    """The binary32 chain is also bitwise independent of (C, sigma) and of the
+    launch shape (block, unroll, software pipelining)."""
     import torch
     from paper_1307_6209_gb300 import sell
 
@@ -75,9 +76,11 @@ def test_mixed_invariant_across_formats():
             h = sell.sell_build(A, C=C, sigma=sigma, store_type=store)
             y = torch.empty(A.nrows, dtype=torch.float32, device="cuda")
             for fl in (0, sell.SELL_SPMV_COMPENSATED):
-                sell.sell_spmv(h, x, y, flags=fl)
-                torch.cuda.synchronize()
-                outs.append(((store, fl), y.cpu().numpy().tobytes()))
+                for block, unroll, pipe in ((256, 4, 0), (128, 8, 1), (512, 1, 1)):
+                    sell.sell_set_launch(h, block, unroll, pipe)
+                    sell.sell_spmv(h, x, y, flags=fl)
+                    torch.cuda.synchronize()
+                    outs.append(((store, fl), y.cpu().numpy().tobytes()))
     by = {}
     for key, b in outs:
         by.setdefault(key, set()).add(b)

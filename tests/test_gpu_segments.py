@@ -76,13 +76,14 @@ def test_f64_rows_match_documented_arithmetic(accumulate):
         _row_result(A.val[A.rpt[i]:A.rpt[i + 1]], x[A.col[A.rpt[i]:A.rpt[i + 1]]], y0[i] if accumulate else 0.0)
         for i in range(A.nrows)])
     flags = sell.SELL_SPMV_ACCUMULATE if accumulate else 0
-    for C, sigma, block in [(32, 1, 256), (32, 10 ** 9, 512), (64, 128, 64), (1, 1, 32), (128, 4, 128)]:
+    for C, sigma, block, pipe in [(32, 1, 256, 0), (32, 10 ** 9, 512, 1), (64, 128, 64, 0), (1, 1, 32, 1),
+                                  (128, 4, 128, 1)]:
         h = sell.sell_build(A, C=C, sigma=sigma)
-        sell.sell_set_launch(h, block, 4)
+        sell.sell_set_launch(h, block, 4, pipe)
         xd = torch.from_numpy(x).cuda()
         yd = torch.from_numpy(y0.copy()).cuda()
         sell.sell_spmv(h, xd, yd, flags=flags)
         torch.cuda.synchronize()
         got = yd.cpu().numpy()
         bad = np.nonzero(got.view(np.uint64) != expect.view(np.uint64))[0]
-        assert bad.size == 0, f"C={C} sigma={sigma}: rows {bad[:8]} (lengths {np.diff(A.rpt)[bad[:8]]})"
+        assert bad.size == 0, f"C={C} sigma={sigma} pipeline={pipe}: rows {bad[:8]} (lengths {np.diff(A.rpt)[bad[:8]]})"

@@ -38,10 +38,10 @@ def test_spmv_matches_oracle_and_is_invariant(name, A):
     first = None
     for C, sigma in [(32, 1), (1, 1), (2, 7), (32, 256), (64, 4096), (128, 10 ** 9), (3, 5000)]:
         h = sell.sell_build(A, C=C, sigma=sigma)
-        for block, unroll in [(256, 4), (128, 1), (512, 8), (64, 2)]:
-            sell.sell_set_launch(h, block, unroll)
+        for block, unroll, pipe in [(256, 4, 0), (128, 1, 1), (512, 8, 0), (64, 2, 1), (256, 8, 1)]:
+            sell.sell_set_launch(h, block, unroll, pipe)
             y = _spmv(h, x)
-            assert np.all(np.abs(y - ref) <= tol_f64(rl, scale)), (C, sigma, block, unroll)
+            assert np.all(np.abs(y - ref) <= tol_f64(rl, scale)), (C, sigma, block, unroll, pipe)
             if first is None:
                 first = y
             assert y.tobytes() == first.tobytes(), "result depends on (C, sigma) or launch shape"
