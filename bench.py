@@ -39,7 +39,8 @@ if ROOT not in sys.path:
 L2_BYTES = 129 * 2 ** 20
 FALLBACK_HBM_GBS = 6800.0
 KERNEL_SOURCES = ["paper_1307_6209_gb300/csrc/sell_spmv_impl.cuh", "paper_1307_6209_gb300/csrc/sell_spmv_f64.cu",
-                  "paper_1307_6209_gb300/csrc/sell_internal.cuh", "paper_1307_6209_gb300/csrc/sell_rowdot.cuh"]
+                  "paper_1307_6209_gb300/csrc/sell_internal.cuh", "paper_1307_6209_gb300/csrc/sell_rowdot.cuh",
+                  "paper_1307_6209_gb300/csrc/sell_spmv_bulk.cuh"]
 
 
 def parse_args():
@@ -52,6 +53,9 @@ def parse_args():
     p.add_argument("--n", type=int, default=None, help="rows (lognormal) or grid edge (stencils)")
     p.add_argument("--C", type=int, default=None)
     p.add_argument("--sigma", type=int, default=None)
+    p.add_argument("--block", type=int, default=None, help="fix the launch block instead of tuning it")
+    p.add_argument("--unroll", type=int, default=None, help="fix the unroll instead of tuning it")
+    p.add_argument("--pipeline", type=int, default=None, help="fix the launch mode (0, 1, 2) instead of tuning it")
     p.add_argument("--no-sweep", action="store_true")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--no-extras", action="store_true", help="skip SpMMV / mixed / e2e extras")
@@ -96,6 +100,17 @@ def kernel_source_hash():
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
+
+
+def kernel_name(best, C, inf):
+    """The binary64 SpMV kernel the tuned launch runs."""
+    long_rows = "true" if inf.max_row_len > 64 else "false"
+    if best.pipeline == 2:
+        ring = {1: 2, 2: 2, 4: 3, 8: 4}[best.unroll]
+        return (f"k_spmv_bulk<double,Plain<double>,{C // 32},{long_rows}> {best.block // 32} warps/block, "
+                f"{ring} pieces per warp")
+    return (f"k_spmmv<double,1,{best.unroll},{'true' if best.pipeline else 'false'},Plain<double>,{long_rows}> "
+            f"block {best.block}")
 
 
 def lookup_traffic(workload_key):
@@ -318,15 +333,18 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ our arm
-def tune_launch(sell, h, xd, yd, stream, flags=0, blocks=(128, 256), unrolls=(1, 2, 4, 8), pipelines=(0, 1)):
+def tune_launch(sell, h, xd, yd, stream, flags=0, blocks=(128, 256), unrolls=(1, 2, 4, 8), pipelines=(0, 1, 2)):
     """Pick (block, unroll, pipeline) for one handle: two interleaved timing
     rounds of every candidate, best of the two; returns (block, unroll,
-    pipeline, seconds)."""
+    pipeline, seconds).  Modes the handle does not support are skipped."""
     cands = [(b, u, p) for b in blocks for u in unrolls for p in pipelines]
     best_t = {c: 1e30 for c in cands}
     for _ in range(2):
         for c in cands:
-            sell.sell_set_launch(h, *c)
+            try:
+                sell.sell_set_launch(h, *c)
+            except sell.SellError:
+                continue
             best_t[c] = min(best_t[c], time_spmv(sell, h, xd, yd, stream, reps=50, flags=flags))
     c, t = min(best_t.items(), key=lambda kv: kv[1])
     sell.sell_set_launch(h, *c)
@@ -614,8 +632,12 @@ def run_ours(args):
             Cs, sigmas = (args.C or 32,), (args.sigma or 1,)
         else:
             Cs, sigmas = sorted({c for c, _ in grid}), sorted({s for _, s in grid})
-        tr = autotune.tune(csr_d, store_type=sell.SELL_F64, Cs=Cs, sigmas=sigmas, blocks=(128, 256, 512),
-                           unrolls=(1, 2, 4, 8), keep=2, stream=stream, use_cache=False, cache=None)
+        blocks = (args.block,) if args.block else (128, 256, 512)
+        unrolls = (args.unroll,) if args.unroll else (1, 2, 4, 8)
+        pipelines = (args.pipeline,) if args.pipeline is not None else (0, 1, 2)
+        tr = autotune.tune(csr_d, store_type=sell.SELL_F64, Cs=Cs, sigmas=sigmas, blocks=blocks,
+                           unrolls=unrolls, pipelines=pipelines, keep=2, stream=stream, use_cache=False,
+                           cache=None)
         best = tr.best
         C, sigma = best.C, best.sigma
         t0 = time.perf_counter()
@@ -726,8 +748,7 @@ def run_ours(args):
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": traffic,
             "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
-            "kernel": (f"k_spmmv<double,1,{best.unroll},{'true' if best.pipeline else 'false'},Plain<double>> "
-                       f"block {best.block}"),
+            "kernel": kernel_name(best, C, inf),
             "kernel_avg_us": round(kern_s * 1e6, 3), "algorithmic_bytes_per_launch": alg}
     nnzr = A.nnz / A.nrows
     bal = model.balance_sell(1.0 / nnzr, inf.beta, nnzr)

@@ -195,13 +195,31 @@ SELL_API sell_status sell_spmmv(sell_handle h, const void *X, int64_t ldx, void 
 SELL_API sell_status sell_spmmv_noalloc(sell_handle h, const void *X, int64_t ldx, void *Y, int64_t ldy,
                                         int32_t k, uint32_t flags, void *stream);
 
-/* Launch tuning of a handle's SpMV/SpMMV kernels (autotuner knob):
- * block = threads per block (32..512, multiple of 32), unroll = entries of a
- * row loaded per step (1, 2, 4 or 8), pipeline = 1 issues the next step's
- * matrix loads before the current step's gathers (software pipelining, for
- * 1 and 2 right-hand sides), 0 does not.  block or unroll 0 and pipeline -1
- * keep the current value.  The results do not depend on any of them. */
+/* Launch tuning of a handle's SpMV/SpMMV kernels (autotuner knob).  The
+ * results do not depend on any of these settings.
+ *   block    threads per block (32..512, multiple of 32); 0 keeps it.
+ *   unroll   entries of a row loaded per step (1, 2, 4 or 8); 0 keeps it.
+ *   pipeline how the matrix stream (val/col) is read; -1 keeps it:
+ *            0 every thread loads its own entries;
+ *            1 as 0, with the next step's loads issued before the current
+ *              step's gathers (software pipelining; 1 and 2 right-hand sides);
+ *            2 bulk-staged: each warp copies whole pieces of its chunks into
+ *              shared memory with asynchronous bulk copies while it multiplies
+ *              the previous piece (single right-hand sides; C = 32, 64 or 128;
+ *              block = warps per block x 32, unroll 1/2/4/8 = 2/2/3/4 pieces
+ *              in flight per warp).  Selecting it computes the per-warp work
+ *              split of the handle on the device (synchronous; a few small
+ *              allocations through the handle's allocator).
+ * Errors: SELL_EINVAL (values), SELL_EUNSUPPORTED (pipeline 2 with another
+ * C, or a block that does not fit on an SM), SELL_ENOMEM, SELL_ECUDA. */
 SELL_API sell_status sell_set_launch(sell_handle h, int32_t block, int32_t unroll, int32_t pipeline);
+
+/* Synchronise `stream`, then report whether a bounded device-side wait in a
+ * kernel of this handle gave up since the last check (SELL_ETIMEOUT; the
+ * products of that launch are incomplete) and clear the record.  Only the
+ * bulk-staged SpMV (pipeline 2) waits on the device.  Errors: SELL_EINVAL,
+ * SELL_ECUDA, SELL_ETIMEOUT. */
+SELL_API sell_status sell_check(sell_handle h, void *stream);
 
 /* Fill *info (host struct).  Errors: SELL_EINVAL. */
 SELL_API sell_status sell_info(sell_handle h, sell_info_t *info);

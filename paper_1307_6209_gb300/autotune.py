@@ -5,7 +5,8 @@ The paper leaves the choice of sigma and of the threads per row to future
 work (Sec. 6) and notes that the best sigma is matrix dependent (Sec. 3.4,
 Sec. 5.3).  Stage 1 builds every (C, sigma) candidate and times the SpMV with
 the default launch; stage 2 sweeps (block, unroll, pipeline) on the best
-formats (pipeline only for 1 and 2 right-hand sides, where it exists).  All
+formats (software pipelining for 1 and 2 right-hand sides, bulk staging for
+single right-hand sides, where they exist).  All
 timing goes through the C ABI (CUDA events on the given stream).  Results are
 cached in a JSON file keyed by a matrix signature (sizes, longest row, the
 coefficient of variation of Eq. "cv", storage type, right-hand sides).
@@ -80,7 +81,7 @@ def _save_cache(path, data):
 
 
 def tune(A, store_type: int = sell.SELL_F64, k: int = 1, Cs=(32, 64, 128), sigmas=None,
-         blocks=(128, 256, 512), unrolls=(1, 2, 4, 8), pipelines=(0, 1), keep: int = 2, reps: int = 30,
+         blocks=(128, 256, 512), unrolls=(1, 2, 4, 8), pipelines=(0, 1, 2), keep: int = 2, reps: int = 30,
          stream=None,
          cache: str | None = DEFAULT_CACHE, use_cache: bool = True) -> TuneResult:
     """Tune the SpMV (k = 1) or SpMMV (k > 1) of CSR matrix A (host numpy or
@@ -127,8 +128,13 @@ def tune(A, store_type: int = sell.SELL_F64, k: int = 1, Cs=(32, 64, 128), sigma
         h = built[(r["C"], r["sigma"])]
         for b in blocks:
             for u in unrolls:
-                for p in (pipelines if k <= 2 else (0,)):
-                    sell.sell_set_launch(h, b, u, p)
+                for p in pipelines:
+                    if (p == 1 and k > 2) or (p == 2 and k > 1):
+                        continue  # modes 1 and 2 exist for k <= 2 and k = 1
+                    try:
+                        sell.sell_set_launch(h, b, u, p)
+                    except sell.SellError:
+                        continue  # e.g. mode 2 with a C it does not take
                     us = _time(lambda: product(h), stream, reps)
                     launches.append({"C": r["C"], "sigma": r["sigma"], "block": b, "unroll": u, "pipeline": p,
                                      "us": us})

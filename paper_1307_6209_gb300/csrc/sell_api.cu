@@ -74,7 +74,8 @@ void free_matrix(sell_matrix *h) {
     // every kernel that may still read the arrays must finish first
     (void)cudaDeviceSynchronize();
     void *ptrs[] = {h->val,    h->col,   h->cs,   h->cl,     h->srl,    h->perm,
-                    h->lchunk, h->lunit, h->cnt, h->cnt2, h->part, h->xstage, h->ystage};
+                    h->lchunk, h->lunit, h->cnt, h->cnt2, h->part, h->xstage, h->ystage,
+                    h->bsc,    h->wsplit, h->dstat};
     for (void *p : ptrs) h->al.put(p, nullptr);
     (void)cudaDeviceSynchronize();
     delete h;
@@ -169,11 +170,37 @@ sell_status sell_set_launch(sell_handle h, int32_t block, int32_t unroll, int32_
         return fail(SELL_EINVAL, "sell_set_launch: block must be a multiple of 32 in [32, 512]");
     if (unroll != 0 && unroll != 1 && unroll != 2 && unroll != 4 && unroll != 8)
         return fail(SELL_EINVAL, "sell_set_launch: unroll must be 1, 2, 4 or 8");
-    if (pipeline < -1 || pipeline > 1) return fail(SELL_EINVAL, "sell_set_launch: pipeline must be -1, 0 or 1");
-    if (block) h->block = block;
-    if (unroll) h->unroll = unroll;
-    if (pipeline >= 0) h->pipeline = pipeline;
+    if (pipeline < -1 || pipeline > 2)
+        return fail(SELL_EINVAL, "sell_set_launch: pipeline must be -1, 0, 1 or 2");
+    const int32_t nb = block ? block : h->block, nu = unroll ? unroll : h->unroll;
+    const int32_t np = pipeline >= 0 ? pipeline : h->pipeline;
+    if (np == 2) {
+        const int32_t ob = h->block, ou = h->unroll;
+        h->block = nb;
+        h->unroll = nu;
+        sell_status st = bulk_prepare(h);
+        if (st != SELL_OK) {
+            h->block = ob;
+            h->unroll = ou;
+            return st;
+        }
+    }
+    h->block = nb;
+    h->unroll = nu;
+    h->pipeline = np;
     return SELL_OK;
+}
+
+sell_status sell_check(sell_handle h, void *stream) {
+    if (!h) return fail(SELL_EINVAL, "sell_check: NULL handle");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    SELL_CUDA_TRY(cudaStreamSynchronize(s));
+    if (!h->dstat) return SELL_OK;
+    int32_t v = 0;
+    SELL_CUDA_TRY(cudaMemcpy(&v, h->dstat, sizeof(v), cudaMemcpyDeviceToHost));
+    if (v == 0) return SELL_OK;
+    SELL_CUDA_TRY(cudaMemset(h->dstat, 0, sizeof(v)));
+    return fail(SELL_ETIMEOUT, "sell_check: a bounded wait of the bulk-staged SpMV gave up");
 }
 
 sell_status sell_info(sell_handle h, sell_info_t *info) {

@@ -349,6 +349,50 @@ __global__ void k_long_units(const int32_t *__restrict__ nseg, const int64_t *__
         for (int32_t sg = 0; sg < nseg[i]; ++sg) lunit[ubase[i] + sg] = make_int2((int)i, sg);
 }
 
+// ------------------------------------------------- bulk-staged SpMV plan
+// bsc[c] = the longest row of at most kSeg entries in chunk c, -1 if the
+// chunk has no such row (the columns of chunk c that the bulk-staged SpMV
+// copies), and its work weight bw[c] = bsc[c] + 1.  One warp per chunk.
+__global__ void k_bulk_cols(const int32_t *__restrict__ srl, int64_t N, int64_t Nc, int C,
+                            int32_t *__restrict__ bsc, int32_t *__restrict__ bw) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t c = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); c < Nc; c += nw) {
+        int m = -1;
+        for (int l = lane; l < C; l += 32) {
+            const int len = srl[c * C + l];
+            if (c * C + l < N && len <= kSeg) m = max(m, len);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) {
+            bsc[c] = m;
+            bw[c] = m + 1;
+        }
+    }
+}
+
+// wsplit[w] = first chunk c with bss[c] >= w * total / nw (bss = exclusive
+// scan of the weights bw, bss[Nc] = total), wsplit[nw] = Nc: warp w stages
+// chunks [wsplit[w], wsplit[w+1]), about total / nw weight.
+__global__ void k_bulk_split(const int64_t *__restrict__ bss, int64_t Nc, int64_t nw, int32_t *__restrict__ wsplit) {
+    const int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (w > nw) return;
+    if (w == nw) {
+        wsplit[w] = (int32_t)Nc;
+        return;
+    }
+    const int64_t total = bss[Nc];
+    const int64_t target = total * w / nw;  // total <= 64 * Nc < 2^37, w <= nw < 2^20
+    int64_t lo = 0, hi = Nc;  // first index in [0, Nc] with bss >= target
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (bss[mid] < target) lo = mid + 1;
+        else hi = mid;
+    }
+    wsplit[w] = (int32_t)lo;
+}
+
 // ------------------------------------------------------------------ scatter
 template <class TI, class TO> __device__ __forceinline__ TO cvt(TI v);
 template <> __device__ __forceinline__ double cvt<double, double>(double v) { return v; }
@@ -689,6 +733,53 @@ sell_status build_format(const sell_csr *A, const sell_opts *o, cudaStream_t s, 
     h->cl = (int32_t *)cl.release_ownership();
     h->srl = (int32_t *)srl.release_ownership();
     h->perm = (int32_t *)perm.release_ownership();
+    return SELL_OK;
+}
+
+// The per-warp work split of the bulk-staged SpMV for nw warps (the per-chunk
+// staged columns are computed on the first call).  Synchronises s.
+sell_status bulk_plan(sell_matrix *h, int64_t nw, cudaStream_t s) {
+    const int64_t Nc = h->nchunks;
+    if (Nc >= INT32_MAX || nw >= (1 << 20)) return fail(SELL_EUNSUPPORTED, "bulk-staged SpMV: plan too large");
+    const Allocator &al = h->al;
+    if (!h->dstat) {
+        void *p = al.get(sizeof(int32_t), s);
+        if (!p) return fail(SELL_ENOMEM, "bulk plan allocation failed");
+        h->dstat = static_cast<int32_t *>(p);
+        SELL_CUDA_TRY(cudaMemsetAsync(h->dstat, 0, sizeof(int32_t), s));
+    }
+    DevBuf bss, bw;
+    if (h->wsplit_n != nw && Nc > 0) {
+        SELL_TRY(bw.alloc(al, Nc * sizeof(int32_t), s));
+        if (!h->bsc) {
+            void *p = al.get(Nc * sizeof(int32_t), s);
+            if (!p) return fail(SELL_ENOMEM, "bulk plan allocation failed");
+            h->bsc = static_cast<int32_t *>(p);
+        }
+        k_bulk_cols<<<grid_for(Nc * 32, 256, 152 * 16), 256, 0, s>>>(h->srl, h->nrows, Nc, h->C, h->bsc,
+                                                                      bw.as<int32_t>());
+        SELL_CUDA_TRY(cudaGetLastError());
+    }
+    if (h->wsplit_n != nw) {
+        if (h->wsplit) {
+            al.put(h->wsplit, s);
+            h->wsplit = nullptr;
+            h->wsplit_n = 0;
+        }
+        void *p = al.get((nw + 1) * sizeof(int32_t), s);
+        if (!p) return fail(SELL_ENOMEM, "bulk plan allocation failed");
+        h->wsplit = static_cast<int32_t *>(p);
+        SELL_TRY(bss.alloc(al, (Nc + 1) * sizeof(int64_t), s));
+        if (Nc > 0) {
+            SELL_TRY(scan_exclusive<int32_t>(bw.as<int32_t>(), 1, Nc, bss.as<int64_t>(), al, s));
+        } else {
+            SELL_CUDA_TRY(cudaMemsetAsync(bss.p, 0, sizeof(int64_t), s));
+        }
+        k_bulk_split<<<grid_for(nw + 1, 256), 256, 0, s>>>(bss.as<int64_t>(), Nc, nw, h->wsplit);
+        SELL_CUDA_TRY(cudaGetLastError());
+        h->wsplit_n = nw;
+    }
+    SELL_CUDA_TRY(cudaStreamSynchronize(s));
     return SELL_OK;
 }
 

@@ -91,6 +91,12 @@ struct sell_matrix {
     int32_t *cnt2 = nullptr;   // nunits * C group counters of very long rows (zero at rest)
     void *part = nullptr;      // segment partials: nunits * C * part_k * 8 bytes
     int32_t part_k = 0;
+    // bulk-staged SpMV (launch mode 2), prepared by sell_set_launch
+    int32_t *bsc = nullptr;    // nchunks staged columns per chunk
+    int32_t *wsplit = nullptr; // wsplit_n + 1 per-warp chunk boundaries
+    int64_t wsplit_n = 0;
+    int32_t *dstat = nullptr;  // device status word: 1 after a bounded wait gave up
+    int32_t bulk_grid = 0, bulk_warps = 0, bulk_ring = 0;
     // host-io staging (lazily allocated)
     void *xstage = nullptr, *ystage = nullptr;
     size_t xstage_bytes = 0, ystage_bytes = 0;
@@ -125,6 +131,8 @@ sell_status launch_block_with_scratch(const sell_matrix *h, const void *X, int64
                                       int64_t ldy, int kb, uint32_t flags, void *part, int32_t *cnt,
                                       int32_t *cnt2, cudaStream_t s);
 sell_status build_format(const sell_csr *A, const sell_opts *o, cudaStream_t s, sell_matrix *h);
+sell_status bulk_plan(sell_matrix *h, int64_t nwarps, cudaStream_t s);
+sell_status bulk_prepare(sell_matrix *h);
 sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s, sell_batch *b);
 sell_status batch_run(sell_batch *b, int32_t grid, cudaStream_t s);
 void batch_release(sell_batch *b, cudaStream_t s);

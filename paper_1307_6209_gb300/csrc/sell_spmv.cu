@@ -15,6 +15,10 @@ cudaError_t spmv_block_f32(const sell_matrix *h, const void *X, int64_t ldx, voi
 cudaError_t spmv_block_bf16(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy, int kb,
                             int acc, int vec, bool comp, void *part, int32_t *cnt, int32_t *cnt2, cudaStream_t s);
 
+int bulk_blocks_per_sm_f64(const sell_matrix *h, int W, int R);
+int bulk_blocks_per_sm_f32(const sell_matrix *h, int W, int R);
+int bulk_blocks_per_sm_bf16(const sell_matrix *h, int W, int R);
+
 namespace {
 
 cudaError_t dispatch(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy, int kb, int acc,
@@ -73,6 +77,39 @@ sell_status launch_block_with_scratch(const sell_matrix *h, const void *X, int64
     const int vec = (((uintptr_t)X % 16) == 0 && ((ldx * xs) % 16) == 0) ? 1 : 0;
     cudaError_t e = dispatch(h, X, ldx, Y, ldy, kb, acc, vec, comp, part, cnt, cnt2, s);
     if (e != cudaSuccess) return cuda_fail(e, "SpMV kernel launch");
+    return SELL_OK;
+}
+
+// Launch shape and work split of the bulk-staged SpMV for the handle's
+// block (warps per block) and unroll (slots per warp: 2, 2, 3, 4 for unroll
+// 1, 2, 4, 8; fewer if shared memory does not hold them): one persistent
+// wave, every SM filled with as many blocks as fit.
+sell_status bulk_prepare(sell_matrix *h) {
+    h->bulk_grid = 0;  // the bulk kernel stays off until the plan below exists
+    if (h->C != 32 && h->C != 64 && h->C != 128)
+        return fail(SELL_EUNSUPPORTED, "bulk-staged SpMV needs C = 32, 64 or 128");
+    // bulk copies need 16-byte aligned sources (chunk offsets are multiples of C)
+    if (((uintptr_t)h->val | (uintptr_t)h->col | (uintptr_t)h->srl) % 16 != 0)
+        return fail(SELL_EUNSUPPORTED, "bulk-staged SpMV needs 16-byte aligned format arrays");
+    const int W = h->block / 32;
+    int R = h->unroll >= 8 ? 4 : (h->unroll >= 4 ? 3 : 2);
+    int bps = 0;
+    for (; R >= 2; --R) {
+        switch (h->store_type) {
+            case SELL_F64: bps = bulk_blocks_per_sm_f64(h, W, R); break;
+            case SELL_F32: bps = bulk_blocks_per_sm_f32(h, W, R); break;
+            default: bps = bulk_blocks_per_sm_bf16(h, W, R); break;
+        }
+        if (bps > 0) break;
+    }
+    if (bps <= 0) return fail(SELL_EUNSUPPORTED, "bulk-staged SpMV: the block does not fit on an SM");
+    int nsm = 0;
+    SELL_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
+    const int grid = nsm * bps;
+    SELL_TRY(bulk_plan(h, (int64_t)grid * W, nullptr));
+    h->bulk_grid = grid;
+    h->bulk_warps = W;
+    h->bulk_ring = R;
     return SELL_OK;
 }
 

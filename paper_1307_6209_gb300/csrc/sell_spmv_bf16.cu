@@ -11,4 +11,11 @@ cudaError_t spmv_block_bf16(const sell_matrix *h, const void *X, int64_t ldx, vo
                 : spmv_block<__nv_bfloat16, Plain<float>>(h, X, ldx, Y, ldy, kb, acc, vec, part, cnt, cnt2, s);
 }
 
+// Resident blocks per SM of the bulk-staged kernels of this storage type.
+int bulk_blocks_per_sm_bf16(const sell_matrix *h, int W, int R) {
+    int a = bulk::blocks_per_sm<__nv_bfloat16, Plain<float>>(h, W, R);
+    int b = bulk::blocks_per_sm<__nv_bfloat16, Dot2>(h, W, R);
+    return a < b ? a : b;
+}
+
 }  // namespace sell

@@ -10,4 +10,10 @@ cudaError_t spmv_block_f64(const sell_matrix *h, const void *X, int64_t ldx, voi
     return spmv_block<double, Plain<double>>(h, X, ldx, Y, ldy, kb, acc, vec, part, cnt, cnt2, s);
 }
 
+// Resident blocks per SM of the bulk-staged kernels of this storage type.
+int bulk_blocks_per_sm_f64(const sell_matrix *h, int W, int R) {
+    int a = bulk::blocks_per_sm<double, Plain<double>>(h, W, R);
+    return a;
+}
+
 }  // namespace sell

@@ -21,6 +21,7 @@
 #pragma once
 
 #include "sell_rowdot.cuh"
+#include "sell_spmv_bulk.cuh"
 
 namespace sell {
 namespace spmv_impl {
@@ -122,7 +123,7 @@ template <class VT, int K, class Acc>
 cudaError_t pick_unroll(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy,
                         int acc, int vec, cudaStream_t s) {
     if constexpr (K <= 2) {
-        if (h->pipeline) return pick_u<VT, K, true, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
+        if (h->pipeline == 1) return pick_u<VT, K, true, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
     }
     return pick_u<VT, K, false, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
 }
@@ -141,11 +142,13 @@ cudaError_t pick_k(const sell_matrix *h, const void *X, int64_t ldx, void *Y, in
 }  // namespace spmv_impl
 
 // Launch one column block (kb in {1, 2, 4, 8}) of the given storage type and
-// accumulation; part/cnt/cnt2 = nullptr uses the handle's scratch.
+// accumulation; part/cnt/cnt2 = nullptr uses the handle's scratch.  A single
+// column with launch mode 2 goes to the bulk-staged kernel.
 template <class VT, class Acc>
 cudaError_t spmv_block(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy, int kb,
                        int acc, int vec, void *part, int32_t *cnt, int32_t *cnt2, cudaStream_t s) {
     using namespace spmv_impl;
+    if (!part && kb == 1 && h->pipeline == 2 && h->bulk_grid > 0) return bulk::run<VT, Acc>(h, X, ldx, Y, ldy, acc, s);
     if (!part) return pick_k<VT, Acc>(h, X, ldx, Y, ldy, kb, acc, vec, s);
     return pick_with<VT, Acc>(h, X, ldx, Y, ldy, kb, acc, vec, part, cnt, cnt2, s);
 }

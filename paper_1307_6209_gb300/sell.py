@@ -76,6 +76,7 @@ SIGNATURES = {
     "sell_spmmv_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32,
                                           ctypes.c_uint32, _P]),
     "sell_set_launch": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "sell_check": (ctypes.c_int, [_P, _P]),
     "sell_info": (ctypes.c_int, [_P, ctypes.POINTER(sell_info_t)]),
     "sell_export": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "sell_free": (ctypes.c_int, [_P]),
@@ -243,6 +244,12 @@ def sell_spmmv_noalloc(h: SellMatrix, X, Y, flags: int = 0, stream=None):
 def sell_set_launch(h: SellMatrix, block: int = 0, unroll: int = 0, pipeline: int = -1):
     """Launch shape of the handle's kernels (0 / -1 keep the current value)."""
     _check(load().sell_set_launch(h.handle, int(block), int(unroll), int(pipeline)))
+
+
+def sell_check(h: SellMatrix, stream=None):
+    """Synchronise the stream; raise SellError(SELL_ETIMEOUT) if a bounded
+    device-side wait of the handle's kernels gave up."""
+    _check(load().sell_check(h.handle, _stream_ptr(stream)))
 
 
 def sell_info(h: SellMatrix) -> Info:

@@ -57,7 +57,10 @@ def test_bad_options_are_einval():
     h = sell.sell_build(synth.laplace2d(8), C=32)
     assert _status(sell.sell_set_launch, h, 48, 0) == sell.SELL_EINVAL
     assert _status(sell.sell_set_launch, h, 0, 3) == sell.SELL_EINVAL
-    assert _status(sell.sell_set_launch, h, 0, 0, 2) == sell.SELL_EINVAL
+    assert _status(sell.sell_set_launch, h, 0, 0, 3) == sell.SELL_EINVAL
+    h1 = sell.sell_build(synth.laplace2d(8), C=16)
+    assert _status(sell.sell_set_launch, h1, 0, 0, 2) == sell.SELL_EUNSUPPORTED
+    sell.sell_check(h1)  # nothing pending, no bounded wait gave up
     assert _status(sell.sell_set_launch, h, 0, 0, -2) == sell.SELL_EINVAL
     lib = sell.load()
     assert lib.sell_spmmv(h.handle, None, 1, None, 1, 0, 0, None) == sell.SELL_EINVAL

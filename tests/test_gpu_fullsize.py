@@ -24,7 +24,8 @@ def lognormal2m():
 
 
 @pytest.mark.parametrize("C,sigma,block,unroll,pipe", [(64, 2_000_000, 128, 4, 1), (32, 2_000_000, 128, 8, 0),
-                                                       (32, 1, 256, 4, 1), (128, 4096, 128, 2, 0)])
+                                                       (32, 1, 256, 4, 1), (128, 4096, 128, 2, 0),
+                                                       (32, 2_000_000, 256, 2, 2), (128, 2_000_000, 512, 4, 2)])
 def test_lognormal_2m_full(lognormal2m, C, sigma, block, unroll, pipe):
     import torch
     from paper_1307_6209_gb300 import sell
@@ -67,6 +68,13 @@ def test_stencil27_200_full():
     ref = oracle.csr_spmv(A, x, nthreads=0)
     scale = oracle.csr_absdot(A, x)
     assert np.all(np.abs(y - ref) <= tol_f64(A.row_lengths(), scale))
+    # the bulk-staged launch mode gives the same bits at full size
+    sell.sell_set_launch(h, 256, 4, 2)
+    yb = torch.full((A.nrows,), float("nan"), dtype=torch.float64, device="cuda")
+    sell.sell_spmv(h, xd, yb)
+    sell.sell_check(h)
+    assert yb.cpu().numpy().tobytes() == y.tobytes()
+    del yb
 
     # structure: SELL-32-1 keeps the original order; the chunk widths are the
     # longest row of every 32 consecutive rows (Eq. "max")

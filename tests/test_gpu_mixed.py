@@ -76,7 +76,7 @@ def test_mixed_invariant_across_formats():
             h = sell.sell_build(A, C=C, sigma=sigma, store_type=store)
             y = torch.empty(A.nrows, dtype=torch.float32, device="cuda")
             for fl in (0, sell.SELL_SPMV_COMPENSATED):
-                for block, unroll, pipe in ((256, 4, 0), (128, 8, 1), (512, 1, 1)):
+                for block, unroll, pipe in ((256, 4, 0), (128, 8, 1), (512, 1, 1), (256, 2, 2), (128, 8, 2)):
                     sell.sell_set_launch(h, block, unroll, pipe)
                     sell.sell_spmv(h, x, y, flags=fl)
                     torch.cuda.synchronize()

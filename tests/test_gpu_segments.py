@@ -77,7 +77,7 @@ def test_f64_rows_match_documented_arithmetic(accumulate):
         for i in range(A.nrows)])
     flags = sell.SELL_SPMV_ACCUMULATE if accumulate else 0
     for C, sigma, block, pipe in [(32, 1, 256, 0), (32, 10 ** 9, 512, 1), (64, 128, 64, 0), (1, 1, 32, 1),
-                                  (128, 4, 128, 1)]:
+                                  (128, 4, 128, 1), (32, 10 ** 9, 256, 2), (64, 1, 128, 2), (128, 128, 512, 2)]:
         h = sell.sell_build(A, C=C, sigma=sigma)
         sell.sell_set_launch(h, block, 4, pipe)
         xd = torch.from_numpy(x).cuda()

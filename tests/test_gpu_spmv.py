@@ -38,9 +38,16 @@ def test_spmv_matches_oracle_and_is_invariant(name, A):
     first = None
     for C, sigma in [(32, 1), (1, 1), (2, 7), (32, 256), (64, 4096), (128, 10 ** 9), (3, 5000)]:
         h = sell.sell_build(A, C=C, sigma=sigma)
-        for block, unroll, pipe in [(256, 4, 0), (128, 1, 1), (512, 8, 0), (64, 2, 1), (256, 8, 1)]:
+        for block, unroll, pipe in [(256, 4, 0), (128, 1, 1), (512, 8, 0), (64, 2, 1), (256, 8, 1),
+                                    (256, 2, 2), (128, 8, 2), (512, 4, 2), (32, 1, 2)]:
+            if pipe == 2 and C not in (32, 64, 128):
+                with pytest.raises(sell.SellError) as e:
+                    sell.sell_set_launch(h, block, unroll, pipe)
+                assert e.value.status == sell.SELL_EUNSUPPORTED
+                continue
             sell.sell_set_launch(h, block, unroll, pipe)
             y = _spmv(h, x)
+            sell.sell_check(h)
             assert np.all(np.abs(y - ref) <= tol_f64(rl, scale)), (C, sigma, block, unroll, pipe)
             if first is None:
                 first = y
@@ -148,4 +155,39 @@ def test_spmv_very_long_rows(shape):
         assert np.all(np.abs(y - ref) <= tol_f64(rl, scale)), (C, sigma)
         first = y if first is None else first
         assert y.tobytes() == first.tobytes()
+        h.free()
+
+
+@pytest.mark.parametrize("name,A", [
+    ("lognormal", synth.lognormal(20011, seed=8, cap=3000)),
+    ("empty_and_long", synth.long_row(5000, 5000, short_len=0, at=100, seed=9)),
+    ("dense", synth.dense(200, 3000, seed=3)),
+    ("random_empty_rows", synth.random_csr(3001, 800, density=0.02, seed=2, empty_rows=0.5)),
+], ids=lambda v: v if isinstance(v, str) else "")
+def test_bulk_staged_bitwise_equal(name, A):
+    """Launch mode 2 (bulk copies into shared memory) gives the bits of mode 0
+    for y = A x, y += A x and the single-column block of a wider product
+    (strided x and y), for every C it supports, with long rows, chunks of
+    empty rows and chunks of long rows only."""
+    import torch
+    from paper_1307_6209_gb300 import sell
+
+    x = synth.vector(A.ncols, seed=11)
+    y0 = synth.vector(A.nrows, seed=12)
+    X = synth.block(A.ncols, 5, seed=13)
+    for C, sigma in [(32, 1), (32, 10 ** 9), (64, 512), (128, 1)]:
+        h = sell.sell_build(A, C=C, sigma=sigma)
+        outs = {}
+        for mode in (0, 2):
+            sell.sell_set_launch(h, 256, 4, mode)
+            y = _spmv(h, x)
+            ya = _spmv(h, x, y0=y0, flags=sell.SELL_SPMV_ACCUMULATE)
+            Xd = torch.from_numpy(X).cuda()
+            Yd = torch.full((A.nrows, 5), float("nan"), dtype=torch.float64, device="cuda")
+            sell.sell_spmmv(h, Xd, Yd)
+            sell.sell_check(h)
+            outs[mode] = (y.tobytes(), ya.tobytes(), Yd.cpu().numpy().tobytes())
+        assert outs[0] == outs[2], (C, sigma)
+        ref, scale, rl = oracle_reference(A, x)
+        assert np.all(np.abs(np.frombuffer(outs[2][0]) - ref) <= tol_f64(rl, scale))
         h.free()
