@@ -142,9 +142,17 @@ SELL_API sell_status sell_build(const sell_csr *A, const sell_opts *opts, void *
 #define SELL_SPMV_ACCUMULATE 0x1u   /* y = y + A x instead of y = A x */
 #define SELL_SPMV_COMPENSATED 0x2u  /* F32/BF16 storage: compensated (Dot2)
                                        binary32 accumulation of each row */
-#define SELL_SPMV_HOST_IO 0x4u      /* x and y (X and Y) are host pointers; the
-                                       copies to and from the handle's staging
-                                       buffers are issued on `stream` */
+#define SELL_SPMV_HOST_IO 0x4u      /* x and y (X and Y) are host pointers
+                                       (pinned for asynchronous copies); the
+                                       copies to and from the handle's two
+                                       staging slots, used in turn, are issued
+                                       on `stream`.  Host-io products of one
+                                       handle run one after another whatever
+                                       their streams, so consecutive calls on
+                                       two streams overlap one call's copies
+                                       with the other's kernels.  The host
+                                       buffers may be reused once the call's
+                                       stream has passed it. */
 
 /* y = A x over the SELL-C-sigma handle (Listing "sell", one GPU thread per
  * row of a chunk, each thread stopping at its own row length -- Sec. 3.4, the

@@ -74,17 +74,20 @@ void free_matrix(sell_matrix *h) {
     // every kernel that may still read the arrays must finish first
     (void)cudaDeviceSynchronize();
     void *ptrs[] = {h->val,    h->col,   h->cs,   h->cl,     h->srl,    h->perm,
-                    h->lchunk, h->lunit, h->cnt, h->cnt2, h->part, h->xstage, h->ystage,
-                    h->bsc,    h->wsplit, h->dstat};
+                    h->lchunk, h->lunit, h->cnt, h->cnt2, h->part, h->io[0].x, h->io[0].y,
+                    h->io[1].x, h->io[1].y, h->bsc, h->wsplit, h->dstat};
     for (void *p : ptrs) h->al.put(p, nullptr);
+    for (auto &sl : h->io)
+        if (sl.done) (void)cudaEventDestroy(sl.done);
+    if (h->kdone) (void)cudaEventDestroy(h->kdone);
     (void)cudaDeviceSynchronize();
     delete h;
 }
 
+// Grow a staging buffer of a slot whose previous use has been waited for.
 sell_status ensure_stage(sell_matrix *h, void **buf, size_t *have, size_t need, cudaStream_t s) {
     if (*have >= need) return SELL_OK;
     if (*buf) {
-        SELL_CUDA_TRY(cudaStreamSynchronize(s));
         h->al.put(*buf, s);
         *buf = nullptr;
         *have = 0;
@@ -147,16 +150,30 @@ sell_status sell_spmmv(sell_handle h, const void *X, int64_t ldx, void *Y, int64
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (!(flags & SELL_SPMV_HOST_IO)) return launch_spmmv(h, X, ldx, Y, ldy, k, flags, s);
 
-    // host buffers: stage through device memory owned by the handle
+    // host buffers: stage through device memory owned by the handle, in two
+    // slots used in turn.  A slot is reused only after its previous
+    // device-to-host copy (event wait on this stream), and the products of
+    // host-io calls run one after another whatever their streams (they share
+    // the long-row scratch), so calls may alternate streams to overlap their
+    // copies with the previous call's kernels.
     const size_t xs = h->store_type == SELL_F64 ? 8 : 4;
     const size_t xb = (size_t)h->ncols * ldx * xs, yb = (size_t)h->nrows * ldy * xs;
-    SELL_TRY(ensure_stage(h, &h->xstage, &h->xstage_bytes, xb > 0 ? xb : 16, s));
-    SELL_TRY(ensure_stage(h, &h->ystage, &h->ystage_bytes, yb, s));
-    if (xb) SELL_CUDA_TRY(cudaMemcpyAsync(h->xstage, X, xb, cudaMemcpyHostToDevice, s));
-    if (flags & SELL_SPMV_ACCUMULATE)
-        SELL_CUDA_TRY(cudaMemcpyAsync(h->ystage, Y, yb, cudaMemcpyHostToDevice, s));
-    SELL_TRY(launch_spmmv(h, h->xstage, ldx, h->ystage, ldy, k, flags & ~SELL_SPMV_HOST_IO, s));
-    SELL_CUDA_TRY(cudaMemcpyAsync(Y, h->ystage, yb, cudaMemcpyDeviceToHost, s));
+    sell_matrix::IoSlot &sl = h->io[h->io_next];
+    if (!sl.done) SELL_CUDA_TRY(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
+    if (!h->kdone) SELL_CUDA_TRY(cudaEventCreateWithFlags(&h->kdone, cudaEventDisableTiming));
+    if (sl.used) SELL_CUDA_TRY(cudaStreamWaitEvent(s, sl.done, 0));
+    SELL_TRY(ensure_stage(h, &sl.x, &sl.xb, xb > 0 ? xb : 16, s));
+    SELL_TRY(ensure_stage(h, &sl.y, &sl.yb, yb, s));
+    h->io_next ^= 1;
+    if (xb) SELL_CUDA_TRY(cudaMemcpyAsync(sl.x, X, xb, cudaMemcpyHostToDevice, s));
+    if (flags & SELL_SPMV_ACCUMULATE) SELL_CUDA_TRY(cudaMemcpyAsync(sl.y, Y, yb, cudaMemcpyHostToDevice, s));
+    if (h->kdone_used) SELL_CUDA_TRY(cudaStreamWaitEvent(s, h->kdone, 0));
+    SELL_TRY(launch_spmmv(h, sl.x, ldx, sl.y, ldy, k, flags & ~SELL_SPMV_HOST_IO, s));
+    SELL_CUDA_TRY(cudaEventRecord(h->kdone, s));
+    h->kdone_used = true;
+    SELL_CUDA_TRY(cudaMemcpyAsync(Y, sl.y, yb, cudaMemcpyDeviceToHost, s));
+    SELL_CUDA_TRY(cudaEventRecord(sl.done, s));
+    sl.used = true;
     return SELL_OK;
 }
 

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "sell.h"
+#include "sell_device.cuh"
 
 namespace sell {
 
@@ -55,14 +56,6 @@ struct DevBuf {
     template <class T> T *as() const { return static_cast<T *>(p); }
 };
 
-// Entries per segment of a long row.  Part of the numerics: a row longer than
-// kSeg is summed segment by segment (sell_rowdot.cuh), so changing it changes
-// the rounding of long rows.
-constexpr int kSeg = 64;
-// Segments per group of the two-level fold of very long rows (more than
-// kSeg * kSuper = 16384 entries); also part of the numerics.
-constexpr int kSuper = 256;
-
 inline size_t value_size(int t) { return t == SELL_F64 ? 8 : (t == SELL_F32 ? 4 : 2); }
 
 }  // namespace sell
@@ -97,9 +90,19 @@ struct sell_matrix {
     int64_t wsplit_n = 0;
     int32_t *dstat = nullptr;  // device status word: 1 after a bounded wait gave up
     int32_t bulk_grid = 0, bulk_warps = 0, bulk_ring = 0;
-    // host-io staging (lazily allocated)
-    void *xstage = nullptr, *ystage = nullptr;
-    size_t xstage_bytes = 0, ystage_bytes = 0;
+    // host-io staging (lazily allocated): two slots used in turn, so that the
+    // copies of one call overlap the kernel of the previous one when calls
+    // alternate streams.  done = recorded after the slot's last device-to-host
+    // copy; kdone = recorded after the latest host-io product's kernels.
+    struct IoSlot {
+        void *x = nullptr, *y = nullptr;
+        size_t xb = 0, yb = 0;
+        cudaEvent_t done = nullptr;
+        bool used = false;
+    } io[2];
+    int io_next = 0;
+    cudaEvent_t kdone = nullptr;
+    bool kdone_used = false;
     size_t device_bytes = 0;
 };
 
@@ -139,40 +142,5 @@ void batch_release(sell_batch *b, cudaStream_t s);
 sell_status bench_read(const void *buf, size_t bytes, double *sink, int32_t grid, cudaStream_t s);
 sell_status bench_fma64(double *sink, int32_t grid, int32_t iters, cudaStream_t s);
 sell_status bench_gather(const void *x, int64_t n, double *sink, int32_t grid, int32_t iters, cudaStream_t s);
-
-// --------------------------------------------------------- device helpers
-// Streaming loads for data touched once per product (val/col): do not allocate
-// in L1 and mark the L2 lines evict-first, so that the gathered vector x keeps
-// its place in L2.
-__device__ __forceinline__ uint64_t l2_evict_first_policy() {
-    uint64_t p;
-    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-
-__device__ __forceinline__ double ld_stream(const double *ptr, uint64_t pol) {
-    double v;
-    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;"
-                 : "=d"(v) : "l"(ptr), "l"(pol));
-    return v;
-}
-__device__ __forceinline__ float ld_stream(const float *ptr, uint64_t pol) {
-    float v;
-    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;"
-                 : "=f"(v) : "l"(ptr), "l"(pol));
-    return v;
-}
-__device__ __forceinline__ int32_t ld_stream(const int32_t *ptr, uint64_t pol) {
-    int32_t v;
-    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;"
-                 : "=r"(v) : "l"(ptr), "l"(pol));
-    return v;
-}
-__device__ __forceinline__ __nv_bfloat16 ld_stream(const __nv_bfloat16 *ptr, uint64_t pol) {
-    unsigned short v;
-    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.b16 %0, [%1], %2;"
-                 : "=h"(v) : "l"(ptr), "l"(pol));
-    return __ushort_as_bfloat16(v);
-}
 
 }  // namespace sell

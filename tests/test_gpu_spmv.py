@@ -99,6 +99,34 @@ def test_spmv_host_io():
     assert y.tobytes() == _spmv(h, x).tobytes()
 
 
+def test_spmv_host_io_alternating_streams():
+    """HOST_IO calls that alternate two streams (the overlapped end-to-end
+    pattern): every call's y is bitwise the device-buffer product of its own
+    x, including rows long enough to use the shared long-row scratch and the
+    accumulate flag."""
+    import torch
+    from paper_1307_6209_gb300 import sell
+
+    A = synth.lognormal(20000, seed=21, cap=3000)
+    h = sell.sell_build(A, C=32, sigma=10 ** 9)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    n = 12
+    xs = [torch.from_numpy(synth.vector(A.ncols, seed=100 + i)).pin_memory() for i in range(n)]
+    y0 = [torch.from_numpy(synth.vector(A.nrows, seed=200 + i)).pin_memory() for i in range(n)]
+    ys = [torch.full((A.nrows,), float("nan"), dtype=torch.float64).pin_memory() for _ in range(n)]
+    for i in range(n):
+        fl = sell.SELL_SPMV_HOST_IO | (sell.SELL_SPMV_ACCUMULATE if i % 3 == 2 else 0)
+        if i % 3 == 2:
+            ys[i].copy_(y0[i])
+        sell.sell_spmv(h, xs[i], ys[i], flags=fl, stream=streams[i % 2])
+    torch.cuda.synchronize()
+    for i in range(n):
+        acc = i % 3 == 2
+        want = _spmv(h, xs[i].numpy(), y0=y0[i].numpy() if acc else None,
+                     flags=sell.SELL_SPMV_ACCUMULATE if acc else 0)
+        assert ys[i].numpy().tobytes() == want.tobytes(), f"call {i}"
+
+
 @pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 8, 11, 16])
 def test_spmmv_columns_bitwise_equal_spmv(k):
     import torch
