@@ -22,7 +22,10 @@
  *   - Index types: row offsets int64, column indices int32 (Sec. 5: four-byte
  *     indices), chunk offsets int64.
  *   - The library allocates its device memory through sell_set_allocator's
- *     callbacks (default: cudaMallocAsync / cudaFreeAsync on the build stream).
+ *     callbacks.  Default: stream-ordered allocation (cudaMallocFromPoolAsync
+ *     / cudaFreeAsync) from one library-owned memory pool per device, which
+ *     keeps freed memory for reuse; sell_free returns the pool's unused
+ *     memory to the device.
  */
 #ifndef SELL_H
 #define SELL_H

@@ -14,7 +14,7 @@ namespace sell {
 namespace {
 thread_local std::string g_last_error;
 std::mutex g_alloc_mu;
-Allocator g_alloc;  // null callbacks = stream-ordered cudaMallocAsync
+Allocator g_alloc;  // null callbacks = stream-ordered allocation from the library pool
 }  // namespace
 
 void set_error(const std::string &msg) { g_last_error = msg; }
@@ -30,10 +30,54 @@ sell_status cuda_fail(cudaError_t e, const char *what) {
     return SELL_ECUDA;
 }
 
+namespace {
+// The default allocator draws from one library-owned memory pool per device.
+// The pool keeps freed memory for reuse (release threshold: unlimited), so
+// plans and staging buffers created in a serving loop do not map new memory
+// each time; sell_free hands the unused part back to the device.
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxDevices] = {};
+
+cudaMemPool_t library_pool(int dev) {
+    if (dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> g(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps pr;
+        std::memset(&pr, 0, sizeof(pr));
+        pr.allocType = cudaMemAllocationTypePinned;
+        pr.handleTypes = cudaMemHandleTypeNone;
+        pr.location.type = cudaMemLocationTypeDevice;
+        pr.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        if (cudaMemPoolCreate(&p, &pr) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t keep = UINT64_MAX;
+        (void)cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pool[dev] = p;
+    }
+    return g_pool[dev];
+}
+}  // namespace
+
+void trim_library_pool(int dev) {
+    cudaMemPool_t p = nullptr;
+    {
+        std::lock_guard<std::mutex> g(g_pool_mu);
+        if (dev >= 0 && dev < kMaxDevices) p = g_pool[dev];
+    }
+    if (p) (void)cudaMemPoolTrimTo(p, 0);
+}
+
 void *Allocator::get(size_t bytes, cudaStream_t s) const {
     if (alloc) return alloc(bytes, ctx, s);
     void *p = nullptr;
-    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+    int dev = 0;
+    cudaMemPool_t pool = cudaGetDevice(&dev) == cudaSuccess ? library_pool(dev) : nullptr;
+    const cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, s) : cudaMallocAsync(&p, bytes, s);
+    if (e != cudaSuccess) {
         (void)cudaGetLastError();  // clear the sticky-free allocation error
         return nullptr;
     }
@@ -80,8 +124,11 @@ void free_matrix(sell_matrix *h) {
     for (auto &sl : h->io)
         if (sl.done) (void)cudaEventDestroy(sl.done);
     if (h->kdone) (void)cudaEventDestroy(h->kdone);
+    const bool own_pool = !h->al.alloc;
+    const int dev = h->device;
     (void)cudaDeviceSynchronize();
     delete h;
+    if (own_pool) trim_library_pool(dev);
 }
 
 // Grow a staging buffer of a slot whose previous use has been waited for.

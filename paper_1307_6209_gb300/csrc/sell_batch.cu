@@ -3,12 +3,13 @@
 // A plan splits every product into column blocks of 8, 4, 2 or 1 right-hand
 // sides and groups the blocks by kernel variant (value type, block width,
 // plain or compensated accumulation).  Each variant present gets one launch
-// (per 192 products): its products travel in the kernel's parameter space and
-// a device table lists the work units -- a unit is kTileRows sorted rows of
-// one product (its short rows), or kTileRows threads of the product's
-// long-row segment units.  One block per unit, long-row units first and
-// biggest products first; the hardware block scheduler balances the uneven
-// products.  (A grid-stride "persistent" form of this kernel was measured:
+// (per 160 products): its products and the block ranges of their work units
+// travel in the kernel's parameter space -- a unit is kTileRows sorted rows
+// of one product (its short rows), or kTileRows threads of the product's
+// long-row segment units.  Creating a plan makes one device allocation (the
+// products' long-row scratch) and no copies, and does not synchronise.  One
+// block per unit, long-row units first and biggest products first; the
+// hardware block scheduler balances the uneven products.  (A grid-stride "persistent" form of this kernel was measured:
 // its loop-carried state raised the register count from 40 to 64, cut the
 // resident blocks per SM from 6 to 4 and made the batch slower.)
 //
@@ -45,23 +46,19 @@ struct Prod {
     int32_t C, kb, type, acc, comp, vec;
 };
 
-// kind 0: a tile of kTileRows sorted rows starting at row idx (short rows);
-// kind 1: kTileRows long-row work-unit threads starting at virtual thread idx.
-struct Unit {
-    int32_t prod;
-    int32_t kind;
-    int64_t idx;
-};
-
 // The products of one launch travel in the kernel's parameter space (read
 // through the constant cache when a unit needs a field), which keeps the
-// register footprint at that of the single-product kernel.
-constexpr int kLaunchProds = 192;  // 192 * 144 B fits the 32 KB parameter limit
+// register footprint at that of the single-product kernel.  The work units
+// need no table: block w belongs to range i of `start` (start[i] <= w <
+// start[i+1]); ranges 0..nprod-1 are the products' long-row units
+// (kTileRows segment threads per block), ranges nprod..2*nprod-1 their short
+// rows (kTileRows rows per block).
+constexpr int kLaunchProds = 160;  // 160 * 152 B + the ranges fit the 32 KB parameter limit
 
 struct LaunchParams {
     Prod prods[kLaunchProds];
-    const Unit *units;
-    int64_t nwork;
+    int32_t start[2 * kLaunchProds + 1];
+    int32_t nprod;
 };
 
 // One block per work unit, long-row units first in the grid so that they
@@ -72,12 +69,19 @@ k_batch(const __grid_constant__ LaunchParams lp) {
     using XT = typename XType<VT>::T;
     constexpr int U = K >= 4 ? 2 : 4;
     const uint64_t pol = l2_evict_first_policy();
-    const int64_t w = blockIdx.x;
-    if (w >= lp.nwork) return;
-    const Unit u = lp.units[w];
-    const Prod &P = lp.prods[u.prod];
-    if (u.kind == 1) {
-        const int64_t v = u.idx + threadIdx.x;
+    const int32_t w = (int32_t)blockIdx.x;
+    if (w >= lp.start[2 * lp.nprod]) return;
+    int lo = 0, hi = 2 * lp.nprod;  // last range with start <= w
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (lp.start[mid] <= w) lo = mid;
+        else hi = mid;
+    }
+    const bool is_long = lo < lp.nprod;
+    const Prod &P = lp.prods[is_long ? lo : lo - lp.nprod];
+    const int64_t first = (int64_t)(w - lp.start[lo]) * kTileRows;
+    if (is_long) {
+        const int64_t v = first + threadIdx.x;
         if (v < P.long_threads)
             long_unit<VT, XT, K, U, false, Acc>(static_cast<const VT *>(P.val), P.col, P.cs, P.srl, P.perm, P.lchunk,
                                          P.lunit, static_cast<Acc *>(P.part), P.cnt, P.cnt2,
@@ -85,7 +89,7 @@ k_batch(const __grid_constant__ LaunchParams lp) {
                                          P.ldx, static_cast<XT *>(P.Y), P.ldy, P.N, P.C, v, P.acc, P.vec != 0, pol);
         return;
     }
-    const int64_t r = u.idx + threadIdx.x;
+    const int64_t r = first + threadIdx.x;
     if (r < P.N)
         short_row<VT, XT, K, U, false, Acc>(static_cast<const VT *>(P.val), P.col, P.cs, P.srl, P.perm,
                                      static_cast<const XT *>(P.X), P.ldx, static_cast<XT *>(P.Y), P.ldy, P.C, r, P.acc,
@@ -160,23 +164,34 @@ sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s
         }
     }
     // each product with long rows gets its own segment scratch and counters,
-    // so products of one plan (even on the same matrix) never share them
+    // so products of one plan (even on the same matrix) never share them; all
+    // of it is one allocation ([partials of every product][counters of every
+    // product]) with one clear of the counters
     b->al = current_allocator();
+    auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+    std::vector<size_t> poff(prods.size(), 0), coff(prods.size(), 0);
+    size_t pbytes = 0, cbytes = 0;
     for (size_t i = 0; i < prods.size(); ++i) {
         const sell_matrix *h = owner[i];
         if (h->nunits == 0) continue;
-        void *p = b->al.get((size_t)h->nunits * h->C * prods[i].kb * 8, s);
-        void *c = p ? b->al.get((size_t)h->nlong * h->C * sizeof(int32_t), s) : nullptr;
-        void *c2 = c ? b->al.get((size_t)h->nunits * h->C * sizeof(int32_t), s) : nullptr;
-        if (p) b->scratch.push_back(p);
-        if (c) b->scratch.push_back(c);
-        if (c2) b->scratch.push_back(c2);
-        if (!p || !c || !c2) return fail(SELL_ENOMEM, "sell_batch_create: segment scratch allocation failed");
-        SELL_CUDA_TRY(cudaMemsetAsync(c, 0, (size_t)h->nlong * h->C * sizeof(int32_t), s));
-        SELL_CUDA_TRY(cudaMemsetAsync(c2, 0, (size_t)h->nunits * h->C * sizeof(int32_t), s));
-        prods[i].part = p;
-        prods[i].cnt = static_cast<int32_t *>(c);
-        prods[i].cnt2 = static_cast<int32_t *>(c2);
+        poff[i] = pbytes;
+        pbytes += up((size_t)h->nunits * h->C * prods[i].kb * 8);
+        coff[i] = cbytes;
+        cbytes += up((size_t)(h->nlong + h->nunits) * h->C * sizeof(int32_t));
+    }
+    if (pbytes + cbytes > 0) {
+        void *blk = b->al.get(pbytes + cbytes, s);
+        if (!blk) return fail(SELL_ENOMEM, "sell_batch_create: segment scratch allocation failed");
+        b->scratch.push_back(blk);
+        char *base = static_cast<char *>(blk);
+        SELL_CUDA_TRY(cudaMemsetAsync(base + pbytes, 0, cbytes, s));
+        for (size_t i = 0; i < prods.size(); ++i) {
+            const sell_matrix *h = owner[i];
+            if (h->nunits == 0) continue;
+            prods[i].part = base + poff[i];
+            prods[i].cnt = reinterpret_cast<int32_t *>(base + pbytes + coff[i]);
+            prods[i].cnt2 = prods[i].cnt + h->nlong * h->C;
+        }
     }
     // group by kernel variant; inside a group: long-row work first, biggest first
     std::map<std::tuple<int, int, int>, std::vector<int32_t>> groups;
@@ -188,26 +203,17 @@ sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s
     b->nprod = (int32_t)prods.size();
     b->nwork = 0;
     std::vector<std::pair<int64_t, int>> order;  // (work, group index) biggest group first
-    std::vector<std::vector<Prod>> gp;
-    std::vector<std::vector<Unit>> gu;
+    std::vector<std::vector<int32_t>> gids;
     std::vector<std::tuple<int, int, int>> gkey;
     for (auto &kv : groups) {
         std::vector<int32_t> ids = kv.second;
         std::stable_sort(ids.begin(), ids.end(), [&](int32_t a, int32_t c) {
             return owner[a]->stored > owner[c]->stored;
         });
-        std::vector<Prod> pv;
-        std::vector<Unit> uv;
-        for (int32_t id : ids) pv.push_back(prods[id]);
-        for (size_t j = 0; j < pv.size(); ++j)
-            for (int64_t v0 = 0; v0 < pv[j].long_threads; v0 += kTileRows) uv.push_back({(int32_t)j, 1, v0});
-        for (size_t j = 0; j < pv.size(); ++j)
-            for (int64_t r0 = 0; r0 < pv[j].N; r0 += kTileRows) uv.push_back({(int32_t)j, 0, r0});
         int64_t work = 0;
-        for (auto &p : pv) work += owner[0] ? p.N * p.kb : 0;
-        order.push_back({work, (int)gp.size()});
-        gp.push_back(std::move(pv));
-        gu.push_back(std::move(uv));
+        for (int32_t id : ids) work += prods[id].N * prods[id].kb;
+        order.push_back({work, (int)gids.size()});
+        gids.push_back(std::move(ids));
         gkey.push_back(kv.first);
     }
     std::stable_sort(order.begin(), order.end(),
@@ -216,27 +222,37 @@ sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s
         const int g = o.second;
         // launches of at most kLaunchProds products each
         KernelFn fn = kernel_for(std::get<0>(gkey[g]), std::get<1>(gkey[g]), std::get<2>(gkey[g]));
-        for (size_t p0 = 0; p0 < gp[g].size(); p0 += kLaunchProds) {
-            const size_t p1 = std::min(gp[g].size(), p0 + (size_t)kLaunchProds);
-            std::vector<Unit> uv;
-            for (const Unit &u : gu[g])
-                if ((size_t)u.prod >= p0 && (size_t)u.prod < p1) uv.push_back({u.prod - (int32_t)p0, u.kind, u.idx});
-            if (uv.empty()) continue;
-            DevBuf du;
-            SELL_TRY(du.alloc(b->al, uv.size() * sizeof(Unit), s));
-            SELL_CUDA_TRY(cudaMemcpyAsync(du.p, uv.data(), uv.size() * sizeof(Unit), cudaMemcpyHostToDevice, s));
-            SELL_CUDA_TRY(cudaStreamSynchronize(s));  // uv goes out of scope below
+        const std::vector<int32_t> &ids = gids[g];
+        for (size_t p0 = 0; p0 < ids.size(); p0 += kLaunchProds) {
+            const int np = (int)(std::min(ids.size(), p0 + (size_t)kLaunchProds) - p0);
             auto *lp = new (std::nothrow) LaunchParams();
             if (!lp) return fail(SELL_ENOMEM, "sell_batch_create: host allocation failed");
-            for (size_t j = p0; j < p1; ++j) lp->prods[j - p0] = gp[g][j];
-            lp->units = static_cast<const Unit *>(du.p);
-            lp->nwork = (int64_t)uv.size();
+            lp->nprod = np;
+            int64_t w = 0;
+            for (int j = 0; j < np; ++j) {  // long-row units of every product first
+                const Prod &P = prods[ids[p0 + j]];
+                lp->prods[j] = P;
+                lp->start[j] = (int32_t)w;
+                w += (P.long_threads + kTileRows - 1) / kTileRows;
+            }
+            for (int j = 0; j < np; ++j) {  // then their short rows
+                lp->start[np + j] = (int32_t)w;
+                w += (prods[ids[p0 + j]].N + kTileRows - 1) / kTileRows;
+            }
+            lp->start[2 * np] = (int32_t)w;
+            if (w > 0x7FFFFFFF) {
+                delete lp;
+                return fail(SELL_EUNSUPPORTED, "sell_batch_create: too many work units in one launch");
+            }
+            if (w == 0) {
+                delete lp;
+                continue;
+            }
             sell_batch::Group G;
             G.fn = reinterpret_cast<void *>(fn);
             G.params = lp;
-            G.nwork = lp->nwork;
-            G.grid = (int32_t)std::min<int64_t>(G.nwork, 0x7FFFFFFF);  // one block per unit
-            G.units = du.release_ownership();
+            G.nwork = w;
+            G.grid = (int32_t)w;  // one block per unit
             b->groups.push_back(G);
             b->nwork += G.nwork;
         }
@@ -245,10 +261,7 @@ sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s
 }
 
 void batch_release(sell_batch *b, cudaStream_t s) {
-    for (auto &G : b->groups) {
-        b->al.put(G.units, s);
-        delete static_cast<LaunchParams *>(G.params);
-    }
+    for (auto &G : b->groups) delete static_cast<LaunchParams *>(G.params);
     b->groups.clear();
     for (void *p : b->scratch) b->al.put(p, s);
     b->scratch.clear();

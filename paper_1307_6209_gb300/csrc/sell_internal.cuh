@@ -109,8 +109,7 @@ struct sell_matrix {
 struct sell_batch {
     struct Group {              // one launch: kernel variant, its products and units
         void *fn = nullptr;     // kernel entry
-        void *params = nullptr; // host copy of the launch parameters (products + unit table pointer)
-        void *units = nullptr;  // device work-unit table
+        void *params = nullptr; // host copy of the launch parameters (products and their unit ranges)
         int64_t nwork = 0;
         int32_t grid = 0;
     };
