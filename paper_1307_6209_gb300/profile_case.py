@@ -1,0 +1,89 @@
+"""Run one configured SpMV / SpMMV case, for profilers and quick timing.
+
+    python -m paper_1307_6209_gb300.profile_case --matrix stencil27 --n 120 --store bf16 \\
+        --C 32 --sigma 1 --block 128 --unroll 8 --pipeline 1 --k 1 --reps 5
+
+builds the synthetic matrix on the device, converts it with the given (C,
+sigma) and storage type, fixes the launch, runs `--warmup` untimed and
+`--reps` timed products on one stream (CUDA events) and prints one JSON line
+with the kernel's average time, GF/s and algorithmic GB/s.  Everything runs
+through the C ABI; nothing is tuned.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+
+def main(argv=None):
+    import torch
+
+    from . import model, sell, synth
+
+    p = argparse.ArgumentParser()
+    p.add_argument("--matrix", choices=["stencil27", "lognormal", "dense", "long_row", "banded"], default="stencil27")
+    p.add_argument("--n", type=int, default=120, help="grid edge (stencil27) or rows")
+    p.add_argument("--store", choices=["f64", "f32", "bf16"], default="f64")
+    p.add_argument("--C", type=int, default=32)
+    p.add_argument("--sigma", type=int, default=1)
+    p.add_argument("--block", type=int, default=128)
+    p.add_argument("--unroll", type=int, default=4)
+    p.add_argument("--pipeline", type=int, default=0)
+    p.add_argument("--k", type=int, default=1)
+    p.add_argument("--compensated", action="store_true")
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--reps", type=int, default=5)
+    a = p.parse_args(argv)
+
+    if a.matrix == "stencil27":
+        A = synth.stencil27_device(a.n, perturb=0.1, seed=0)
+    elif a.matrix == "lognormal":
+        A = synth.lognormal_device(a.n, seed=0)
+    elif a.matrix == "dense":
+        A = synth.dense_device(a.n)
+    elif a.matrix == "long_row":
+        A = synth.long_row_device(a.n, a.n, short_len=3, at=a.n // 3)
+    else:
+        A = synth.banded_device(a.n, seed=0)
+    st = {"f64": sell.SELL_F64, "f32": sell.SELL_F32, "bf16": sell.SELL_BF16}[a.store]
+    dt = torch.float64 if st == sell.SELL_F64 else torch.float32
+    s = torch.cuda.Stream()
+    h = sell.sell_build(A, C=a.C, sigma=a.sigma, store_type=st, stream=s)
+    sell.sell_set_launch(h, a.block, a.unroll, a.pipeline)
+    g = torch.Generator("cuda").manual_seed(0)
+    X = torch.rand((A.ncols, a.k), dtype=dt, device="cuda", generator=g) * 2 - 1
+    Y = torch.empty((A.nrows, a.k), dtype=dt, device="cuda")
+    x1, y1 = X[:, 0].contiguous(), Y[:, 0].contiguous()
+    flags = sell.SELL_SPMV_COMPENSATED if a.compensated else 0
+
+    def step():
+        if a.k == 1:
+            sell.sell_spmv(h, x1, y1, flags=flags, stream=s)
+        else:
+            sell.sell_spmmv(h, X, Y, flags=flags, stream=s)
+
+    for _ in range(a.warmup):
+        step()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.reps)]
+    for e0, e1 in ev:
+        e0.record(s)
+        step()
+        e1.record(s)
+    torch.cuda.synchronize()
+    sell.sell_check(h, stream=s)
+    us = sum(e0.elapsed_time(e1) for e0, e1 in ev) * 1e3 / a.reps
+    inf = h.info
+    vb = {sell.SELL_F64: 8, sell.SELL_F32: 4}.get(st, 2)
+    xb = 8 if st == sell.SELL_F64 else 4
+    alg = model.algorithmic_bytes(inf.nrows, inf.ncols, inf.nnz, inf.nchunks, a.C, vb, xb, inf.has_perm, k=a.k)
+    print(json.dumps({"matrix": a.matrix, "n": a.n, "nrows": inf.nrows, "nnz": inf.nnz, "store": a.store,
+                      "C": a.C, "sigma": a.sigma, "beta": round(inf.beta, 6), "block": a.block,
+                      "unroll": a.unroll, "pipeline": a.pipeline, "k": a.k, "us": round(us, 3),
+                      "gflops": round(2.0 * inf.nnz * a.k / us / 1e3, 1),
+                      "algorithmic_gbs": round(alg / us / 1e3, 1), "value_bytes": vb}))
+    h.free()
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())
