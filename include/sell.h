@@ -268,18 +268,18 @@ typedef struct sell_batch *sell_batch_plan;
 
 /* Prepare a batch of n products to run in a few launches (one per kernel
  * variant present -- value type, block of 1/2/4/8 right-hand sides, plain or
- * compensated accumulation -- and per 192 products).  Work units are tiles of
+ * compensated accumulation -- and per 160 products).  Work units are tiles of
  * 256 sorted rows of one product, or 256 threads of its long-row segment
  * work; every launch has one block per unit, long-row work first and the
  * biggest products first.  The products may use matrices of different sizes
  * and storage types; a matrix with more than 8 right-hand sides is split
  * into blocks of 8.  Each result is bit-identical to the same product run
- * alone by sell_spmmv.  The plan owns its device tables and the long-row
- * scratch of its products (so plans never share scratch with each other or
- * with sell_spmmv); the items' buffers are referenced, not copied.  Several
- * products in one plan must not write overlapping Y.  Synchronises `stream`
- * (after uploading the tables).  Errors: SELL_EINVAL, SELL_ENOMEM,
- * SELL_ECUDA. */
+ * alone by sell_spmmv.  The plan owns the long-row scratch of its products
+ * (one allocation, cleared on `stream`; plans never share scratch with each
+ * other or with sell_spmmv); the work units travel in the launch parameters;
+ * the items' buffers are referenced, not copied.  Several products in one
+ * plan must not write overlapping Y.  Does not synchronise.  Errors:
+ * SELL_EINVAL, SELL_ENOMEM, SELL_ECUDA. */
 SELL_API sell_status sell_batch_create(const sell_batch_item *items, int32_t n, void *stream,
                               sell_batch_plan *out);
 
@@ -291,6 +291,75 @@ SELL_API sell_status sell_batch_run(sell_batch_plan plan, int32_t grid, void *st
  * the stream of the plan's latest sell_batch_run (no host wait); a plan run
  * on several streams must have finished its runs on the other streams. */
 SELL_API sell_status sell_batch_free(sell_batch_plan plan);
+
+/* ------------------------------------------------------------- serving */
+
+/* A continuous-batching server over device-resident handles (an extension;
+ * the paper stops at single products).  Requests Y = A_mid X arrive from any
+ * thread.  A scheduler thread admits them in arrival order while their device
+ * footprint -- the x block, the y block and the long-row scratch -- fits in
+ * an arena of budget - resident bytes (allocated once at creation, so the
+ * budget is never exceeded), packs the admitted ones into one batch plan
+ * (sell_batch_create) on a free stream with the host-to-device copies before
+ * it and the device-to-host copies after it, and keeps up to `streams`
+ * batches in flight: requests that arrive while others run are admitted as
+ * soon as a stream and memory are free, and their work overlaps on the
+ * device.  Every result is bitwise the result of the same product alone. */
+typedef struct sell_server *sell_server_t;
+
+typedef struct {
+    int64_t budget_bytes; /* device bytes for the resident handles plus all requests in flight */
+    int32_t max_batch;    /* requests per batch, 1..4096 */
+    int32_t streams;      /* batches in flight, 1..16 */
+} sell_server_opts;
+
+typedef struct {
+    double t_arrive, t_launch, t_done; /* seconds, steady clock (differences are latencies) */
+    int32_t batch;                     /* requests in the batch it ran in */
+    int32_t status;                    /* SELL_OK or the error of its batch */
+} sell_request_info;
+
+typedef struct {
+    int64_t requests, batches, batched_requests, queued;
+    int64_t resident_bytes, budget_bytes, in_use_bytes, peak_bytes; /* peak: resident + arena high-water mark */
+} sell_server_stats_t;
+
+/* Start a server over n handles (all on the current device; they must
+ * outlive the server).  Errors: SELL_EINVAL (arguments, handles that fill the
+ * budget), SELL_ENOMEM, SELL_ECUDA. */
+SELL_API sell_status sell_server_create(const sell_handle *mats, int32_t n, const sell_server_opts *opts,
+                                        sell_server_t *out);
+
+/* Queue Y = A_mid X for k right-hand sides (row-major ncols x k and
+ * nrows x k, binary64 for F64 handles, binary32 otherwise).  X is page-locked
+ * host memory that stays unchanged until the request completes; Y is
+ * page-locked host memory that receives the result, or NULL to keep the
+ * result on the device (sell_server_result) until sell_server_release.
+ * flags: SELL_SPMV_ACCUMULATE (host Y only: Y = Y + A X),
+ * SELL_SPMV_COMPENSATED.  Does not block.  *id names the request.  Errors:
+ * SELL_EINVAL (bad id/k/flags, pageable memory, a request larger than the
+ * budget), SELL_EUNSUPPORTED, SELL_ENOMEM. */
+SELL_API sell_status sell_server_submit(sell_server_t srv, int32_t mid, const void *X, int32_t k, void *Y,
+                                        uint32_t flags, uint64_t *id);
+
+/* Block until request id has completed (or timeout_s passed: SELL_ETIMEOUT)
+ * and fill *info (may be NULL).  A request with a host Y is forgotten after
+ * its wait; a device-result request stays until sell_server_release.
+ * Errors: SELL_EINVAL (unknown id), SELL_ETIMEOUT, the batch's error. */
+SELL_API sell_status sell_server_wait(sell_server_t srv, uint64_t id, double timeout_s, sell_request_info *info);
+
+/* Device address of a completed device-result request's Y (nrows x k). */
+SELL_API sell_status sell_server_result(sell_server_t srv, uint64_t id, void **dev_y);
+
+/* Return a completed device-result request's Y to the arena. */
+SELL_API sell_status sell_server_release(sell_server_t srv, uint64_t id);
+
+/* Counters and the device-memory high-water mark. */
+SELL_API sell_status sell_server_stats(sell_server_t srv, sell_server_stats_t *stats);
+
+/* Finish every queued and running request, stop the scheduler and free the
+ * server (NULL accepted). */
+SELL_API sell_status sell_server_destroy(sell_server_t srv);
 
 /* ------------------------------------------------------------ measuring */
 

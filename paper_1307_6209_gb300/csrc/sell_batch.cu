@@ -116,9 +116,48 @@ KernelFn kernel_for(int type, int comp, int kb) {
 
 }  // namespace
 
-sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s, sell_batch *b) {
+namespace {
+size_t up256(size_t x) { return (x + 255) / 256 * 256; }
+int block_width(int rem) { return rem >= 8 ? 8 : rem >= 4 ? 4 : rem >= 2 ? 2 : 1; }
+}  // namespace
+
+// Long-row scratch of one batch item (all its column blocks): the segment
+// partials of every block, then the counters of every block (cleared
+// together).  0 for matrices without long rows.
+size_t batch_item_scratch(const sell_matrix *h, int32_t k, size_t *counter_offset) {
+    size_t pb = 0, cb = 0;
+    if (h->nunits > 0 && h->nrows > 0) {
+        for (int32_t done = 0; done < k;) {
+            const int kb = block_width(k - done);
+            pb += up256((size_t)h->nunits * h->C * kb * 8);
+            cb += up256((size_t)(h->nlong + h->nunits) * h->C * sizeof(int32_t));
+            done += kb;
+        }
+    }
+    if (counter_offset) *counter_offset = pb;
+    return pb + cb;
+}
+
+sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s, sell_batch *b,
+                         void *const *scratch) {
     std::vector<Prod> prods;
     std::vector<const sell_matrix *> owner;
+    b->al = current_allocator();
+    // each item with long rows gets its own scratch (given by the caller, or
+    // one allocation for the whole plan), so products of one plan -- even on
+    // the same matrix -- never share segment partials or counters
+    char *own = nullptr;
+    if (!scratch) {
+        size_t total = 0;
+        for (int32_t i = 0; i < n; ++i)
+            if (items[i].A && items[i].k >= 1) total += batch_item_scratch(items[i].A, items[i].k, nullptr);
+        if (total > 0) {
+            own = static_cast<char *>(b->al.get(total, s));
+            if (!own) return fail(SELL_ENOMEM, "sell_batch_create: segment scratch allocation failed");
+            b->scratch.push_back(own);
+        }
+    }
+    size_t own_off = 0;
     for (int32_t i = 0; i < n; ++i) {
         const sell_batch_item &it = items[i];
         const sell_matrix *h = it.A;
@@ -131,10 +170,19 @@ sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s
         if ((it.flags & SELL_SPMV_COMPENSATED) && h->store_type == SELL_F64)
             return fail(SELL_EUNSUPPORTED, "compensated accumulation needs F32/BF16 storage");
         if (h->nrows == 0) continue;
+        size_t coff = 0;
+        const size_t sbytes = batch_item_scratch(h, it.k, &coff);
+        char *sc = nullptr;
+        if (sbytes > 0) {
+            sc = scratch ? static_cast<char *>(scratch[i]) : own + own_off;
+            own_off += scratch ? 0 : sbytes;
+            if (!sc) return fail(SELL_EINVAL, "sell_batch_create: missing scratch");
+            SELL_CUDA_TRY(cudaMemsetAsync(sc + coff, 0, sbytes - coff, s));
+        }
+        size_t poff = 0, cpos = coff;
         const size_t xs = h->store_type == SELL_F64 ? 8 : 4;
         for (int32_t done = 0; done < it.k;) {
-            int rem = it.k - done;
-            int kb = rem >= 8 ? 8 : rem >= 4 ? 4 : rem >= 2 ? 2 : 1;
+            const int kb = block_width(it.k - done);
             Prod P;
             P.val = h->val;
             P.col = h->col;
@@ -145,6 +193,13 @@ sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s
             P.part = nullptr;
             P.cnt = nullptr;
             P.cnt2 = nullptr;
+            if (sc) {
+                P.part = sc + poff;
+                P.cnt = reinterpret_cast<int32_t *>(sc + cpos);
+                P.cnt2 = P.cnt + h->nlong * h->C;
+                poff += up256((size_t)h->nunits * h->C * kb * 8);
+                cpos += up256((size_t)(h->nlong + h->nunits) * h->C * sizeof(int32_t));
+            }
             P.long_threads = h->nunits * h->C;
             P.perm = (h->flags & SELL_BUILD_PERMUTE_COLS) ? nullptr : h->perm;
             P.X = static_cast<const char *>(it.X) + done * xs;
@@ -161,36 +216,6 @@ sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s
             prods.push_back(P);
             owner.push_back(h);
             done += kb;
-        }
-    }
-    // each product with long rows gets its own segment scratch and counters,
-    // so products of one plan (even on the same matrix) never share them; all
-    // of it is one allocation ([partials of every product][counters of every
-    // product]) with one clear of the counters
-    b->al = current_allocator();
-    auto up = [](size_t x) { return (x + 255) / 256 * 256; };
-    std::vector<size_t> poff(prods.size(), 0), coff(prods.size(), 0);
-    size_t pbytes = 0, cbytes = 0;
-    for (size_t i = 0; i < prods.size(); ++i) {
-        const sell_matrix *h = owner[i];
-        if (h->nunits == 0) continue;
-        poff[i] = pbytes;
-        pbytes += up((size_t)h->nunits * h->C * prods[i].kb * 8);
-        coff[i] = cbytes;
-        cbytes += up((size_t)(h->nlong + h->nunits) * h->C * sizeof(int32_t));
-    }
-    if (pbytes + cbytes > 0) {
-        void *blk = b->al.get(pbytes + cbytes, s);
-        if (!blk) return fail(SELL_ENOMEM, "sell_batch_create: segment scratch allocation failed");
-        b->scratch.push_back(blk);
-        char *base = static_cast<char *>(blk);
-        SELL_CUDA_TRY(cudaMemsetAsync(base + pbytes, 0, cbytes, s));
-        for (size_t i = 0; i < prods.size(); ++i) {
-            const sell_matrix *h = owner[i];
-            if (h->nunits == 0) continue;
-            prods[i].part = base + poff[i];
-            prods[i].cnt = reinterpret_cast<int32_t *>(base + pbytes + coff[i]);
-            prods[i].cnt2 = prods[i].cnt + h->nlong * h->C;
         }
     }
     // group by kernel variant; inside a group: long-row work first, biggest first

@@ -135,7 +135,11 @@ sell_status launch_block_with_scratch(const sell_matrix *h, const void *X, int64
 sell_status build_format(const sell_csr *A, const sell_opts *o, cudaStream_t s, sell_matrix *h);
 sell_status bulk_plan(sell_matrix *h, int64_t nwarps, cudaStream_t s);
 sell_status bulk_prepare(sell_matrix *h);
-sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s, sell_batch *b);
+// scratch: per item, batch_item_scratch() bytes of device memory (or NULL for
+// items without long rows); NULL: the plan allocates its own.
+sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s, sell_batch *b,
+                         void *const *scratch = nullptr);
+size_t batch_item_scratch(const sell_matrix *h, int32_t k, size_t *counter_offset);
 sell_status batch_run(sell_batch *b, int32_t grid, cudaStream_t s);
 void batch_release(sell_batch *b, cudaStream_t s);
 sell_status bench_read(const void *buf, size_t bytes, double *sink, int32_t grid, cudaStream_t s);

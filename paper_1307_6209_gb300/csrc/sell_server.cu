@@ -1,0 +1,513 @@
+// sell_server.cu -- continuous-batching SpMV/SpMMV server over device-resident
+// SELL-C-sigma matrices (an extension: the paper stops at single products).
+//
+// Requests (matrix, block of right-hand sides in pinned host memory) arrive at
+// any time from any thread.  One scheduler thread per server:
+//   * admits queued requests in arrival order while their device footprint
+//     (x block, y block, long-row scratch) fits in an arena of
+//     budget - resident bytes -- the HBM budget is never exceeded;
+//   * packs the admitted ones into one batch plan (sell_batch.cu: one launch
+//     per kernel variant, every product bitwise the same as alone) on a free
+//     stream, with the host-to-device copies of the x blocks before it and
+//     the device-to-host copies of the results after it;
+//   * keeps up to `streams` batches in flight, so requests that arrive while
+//     others run are admitted as soon as a stream and memory are free and
+//     their work overlaps on the device;
+//   * retires a batch when its completion event has passed: stamps the
+//     requests, returns their memory to the arena and wakes their waiters.
+// Times are seconds on a steady clock shared by all requests of the process.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "sell_internal.cuh"
+
+namespace sell {
+namespace {
+
+double now_s() {
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+size_t round256(size_t x) { return (x + 255) / 256 * 256; }
+// Arena bytes of one region of n bytes (empty regions still take one block, so
+// that every request owns distinct addresses).
+size_t region(size_t n) { return round256(n ? n : 1); }
+
+// First-fit sub-allocator of one device buffer; blocks are 256-byte aligned
+// and freed blocks merge with their free neighbours.
+class Arena {
+   public:
+    void reset(size_t size) {
+        free_.clear();
+        if (size) free_[0] = size;
+    }
+    bool alloc(size_t n, size_t *off) {
+        n = round256(n);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < n) continue;
+            *off = it->first;
+            const size_t rest = it->second - n, o = it->first;
+            free_.erase(it);
+            if (rest) free_[o + n] = rest;
+            return true;
+        }
+        return false;
+    }
+    void release(size_t off, size_t n) {
+        n = round256(n);
+        auto it = free_.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+
+   private:
+    std::map<size_t, size_t> free_;
+};
+
+enum ReqState { kQueued = 0, kRunning = 1, kDone = 2 };
+
+struct Req {
+    uint64_t id = 0;
+    int32_t mid = 0, k = 1;
+    uint32_t flags = 0;
+    const void *X = nullptr;  // host
+    void *Y = nullptr;        // host, or null: the result stays on the device
+    size_t xb = 0, yb = 0, sb = 0, xoff = 0, yoff = 0, soff = 0;
+    bool reserved = false;
+    double ta = 0, tl = 0, td = 0;
+    int state = kQueued;
+    int32_t status = SELL_OK, batch = 0;
+    bool keep_y() const { return Y == nullptr; }
+};
+
+struct Batch {
+    int si = 0;
+    sell_batch *plan = nullptr;
+    std::vector<Req *> reqs;
+};
+
+bool is_pinned_host(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+}  // namespace
+}  // namespace sell
+
+struct sell_server {
+    std::vector<sell_matrix *> mats;
+    int device = 0;
+    int64_t budget = 0, resident = 0, arena_bytes = 0, used = 0, peak_used = 0;
+    int32_t max_batch = 64, nstreams = 3;
+    sell::Allocator al;
+    char *arena_base = nullptr;
+    sell::Arena arena;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> events;  // one per stream (a stream holds at most one batch)
+    std::deque<int> free_streams;
+    std::vector<sell::Batch> inflight;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<sell::Req *> queue;
+    std::unordered_map<uint64_t, sell::Req *> reqs;
+    uint64_t next_id = 1;
+    int64_t nreq = 0, nbatch = 0, nbatched = 0;
+    bool stop = false;
+    std::thread thr;
+};
+
+namespace sell {
+namespace {
+
+// Device footprint of a request: its x and y blocks and its long-row scratch.
+void sizes(const sell_server *S, Req *r) {
+    const sell_matrix *h = S->mats[r->mid];
+    const size_t es = h->store_type == SELL_F64 ? 8 : 4;
+    r->xb = (size_t)h->ncols * r->k * es;
+    r->yb = (size_t)h->nrows * r->k * es;
+    r->sb = batch_item_scratch(h, r->k, nullptr);
+}
+
+size_t footprint(const Req *r) { return region(r->xb) + region(r->yb) + (r->sb ? round256(r->sb) : 0); }
+
+bool reserve(sell_server *S, Req *r) {
+    size_t xo = 0, yo = 0, so = 0;
+    if (!S->arena.alloc(region(r->xb), &xo)) return false;
+    if (!S->arena.alloc(region(r->yb), &yo)) {
+        S->arena.release(xo, region(r->xb));
+        return false;
+    }
+    if (r->sb && !S->arena.alloc(r->sb, &so)) {
+        S->arena.release(xo, region(r->xb));
+        S->arena.release(yo, region(r->yb));
+        return false;
+    }
+    r->xoff = xo;
+    r->yoff = yo;
+    r->soff = so;
+    r->reserved = true;
+    S->used += (int64_t)footprint(r);
+    S->peak_used = std::max(S->peak_used, S->used);
+    return true;
+}
+
+void release_x_s(sell_server *S, Req *r) {
+    S->arena.release(r->xoff, region(r->xb));
+    S->used -= (int64_t)region(r->xb);
+    if (r->sb) {
+        S->arena.release(r->soff, r->sb);
+        S->used -= (int64_t)round256(r->sb);
+    }
+}
+
+void release_y(sell_server *S, Req *r) {
+    S->arena.release(r->yoff, region(r->yb));
+    S->used -= (int64_t)region(r->yb);
+    r->reserved = false;
+}
+
+// Issue one batch on stream si (called without the lock; the requests are
+// owned by the scheduler until they are marked done).
+void launch(sell_server *S, int si, std::vector<Req *> &batch, Batch &B) {
+    cudaStream_t st = S->streams[si];
+    const double t = now_s();
+    const int n = (int)batch.size();
+    std::vector<sell_batch_item> items(n);
+    std::vector<void *> scr(n, nullptr);
+    sell_status status = SELL_OK;
+    for (int i = 0; i < n; ++i) {
+        Req *r = batch[i];
+        r->tl = t;
+        r->batch = n;
+        sell_matrix *h = S->mats[r->mid];
+        char *xd = S->arena_base + r->xoff, *yd = S->arena_base + r->yoff;
+        if (r->xb && status == SELL_OK &&
+            cudaMemcpyAsync(xd, r->X, r->xb, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            status = cuda_fail(cudaGetLastError(), "server: input copy");
+        if ((r->flags & SELL_SPMV_ACCUMULATE) && r->yb && status == SELL_OK &&
+            cudaMemcpyAsync(yd, r->Y, r->yb, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            status = cuda_fail(cudaGetLastError(), "server: accumulate copy");
+        items[i].A = h;
+        items[i].X = xd;
+        items[i].Y = yd;
+        items[i].ldx = r->k;
+        items[i].ldy = r->k;
+        items[i].k = r->k;
+        items[i].flags = r->flags;
+        scr[i] = r->sb ? S->arena_base + r->soff : nullptr;
+    }
+    B.si = si;
+    B.reqs = batch;
+    B.plan = new (std::nothrow) sell_batch();
+    if (!B.plan && status == SELL_OK) status = SELL_ENOMEM;
+    if (status == SELL_OK) status = batch_create(items.data(), n, st, B.plan, scr.data());
+    if (status == SELL_OK) status = batch_run(B.plan, 0, st);
+    for (int i = 0; i < n && status == SELL_OK; ++i) {
+        Req *r = batch[i];
+        if (!r->keep_y() && r->yb &&
+            cudaMemcpyAsync(r->Y, S->arena_base + r->yoff, r->yb, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            status = cuda_fail(cudaGetLastError(), "server: result copy");
+    }
+    if (status != SELL_OK)
+        for (Req *r : batch) r->status = status;
+    if (cudaEventRecord(S->events[si], st) != cudaSuccess) {
+        (void)cudaGetLastError();
+        (void)cudaStreamSynchronize(st);
+    }
+}
+
+void scheduler(sell_server *S) {
+    (void)cudaSetDevice(S->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    for (;;) {
+        // retire finished batches
+        bool retired = false;
+        for (size_t i = 0; i < S->inflight.size();) {
+            Batch &B = S->inflight[i];
+            const cudaError_t q = cudaEventQuery(S->events[B.si]);
+            if (q == cudaErrorNotReady) {
+                ++i;
+                continue;
+            }
+            if (q != cudaSuccess) (void)cudaGetLastError();
+            const double t = now_s();
+            for (Req *r : B.reqs) {
+                r->td = t;
+                if (q != cudaSuccess && r->status == SELL_OK) r->status = SELL_ECUDA;
+                release_x_s(S, r);
+                if (!r->keep_y() || r->status != SELL_OK) release_y(S, r);
+                r->state = kDone;
+            }
+            if (B.plan) {
+                batch_release(B.plan, S->streams[B.si]);
+                delete B.plan;
+            }
+            S->free_streams.push_back(B.si);
+            S->inflight.erase(S->inflight.begin() + i);
+            retired = true;
+        }
+        if (retired) S->cv_done.notify_all();
+        // admit in arrival order while the footprint fits, then launch
+        if (!S->free_streams.empty() && !S->queue.empty()) {
+            std::vector<Req *> batch;
+            while (!S->queue.empty() && (int)batch.size() < S->max_batch) {
+                Req *r = S->queue.front();
+                if (!reserve(S, r)) break;
+                S->queue.pop_front();
+                r->state = kRunning;
+                batch.push_back(r);
+            }
+            if (!batch.empty()) {
+                const int si = S->free_streams.front();
+                S->free_streams.pop_front();
+                Batch B;
+                lk.unlock();
+                launch(S, si, batch, B);
+                lk.lock();
+                // (requests of a batch are retired together once its event passed)
+                S->inflight.push_back(std::move(B));
+                S->nbatch += 1;
+                S->nbatched += (int64_t)batch.size();
+                continue;
+            }
+        }
+        if (S->stop && S->queue.empty() && S->inflight.empty()) break;
+        if (S->inflight.empty())
+            S->cv_work.wait(lk);  // idle: until a submit, a release or stop
+        else
+            S->cv_work.wait_for(lk, std::chrono::microseconds(20));  // poll the events
+    }
+}
+
+}  // namespace
+}  // namespace sell
+
+using namespace sell;
+
+extern "C" {
+
+sell_status sell_server_create(const sell_handle *mats, int32_t n, const sell_server_opts *o, sell_server_t *out) {
+    if (!mats || n < 1 || !o || !out) return fail(SELL_EINVAL, "sell_server_create: bad arguments");
+    if (o->max_batch < 1 || o->max_batch > 4096 || o->streams < 1 || o->streams > 16)
+        return fail(SELL_EINVAL, "sell_server_create: need 1 <= max_batch <= 4096 and 1 <= streams <= 16");
+    sell_server *S = new (std::nothrow) sell_server();
+    if (!S) return fail(SELL_ENOMEM, "sell_server_create: host allocation failed");
+    int dev = 0;
+    (void)cudaGetDevice(&dev);
+    S->device = dev;
+    for (int32_t i = 0; i < n; ++i) {
+        if (!mats[i]) {
+            delete S;
+            return fail(SELL_EINVAL, "sell_server_create: NULL matrix");
+        }
+        if (mats[i]->device != dev) {
+            delete S;
+            return fail(SELL_EINVAL, "sell_server_create: matrices must live on the current device");
+        }
+        S->mats.push_back(mats[i]);
+        S->resident += (int64_t)mats[i]->device_bytes;
+    }
+    S->budget = o->budget_bytes;
+    if (S->resident >= S->budget) {
+        delete S;
+        return fail(SELL_EINVAL, "sell_server_create: the resident matrices fill the budget");
+    }
+    S->arena_bytes = (S->budget - S->resident) / 256 * 256;
+    S->max_batch = o->max_batch;
+    S->nstreams = o->streams;
+    S->al = current_allocator();
+    S->arena_base = static_cast<char *>(S->al.get((size_t)S->arena_bytes, nullptr));
+    if (!S->arena_base) {
+        delete S;
+        return fail(SELL_ENOMEM, "sell_server_create: arena allocation failed");
+    }
+    S->arena.reset((size_t)S->arena_bytes);
+    sell_status st = SELL_OK;
+    for (int i = 0; i < S->nstreams && st == SELL_OK; ++i) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t e = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+            st = cuda_fail(cudaGetLastError(), "sell_server_create: stream/event");
+        S->streams.push_back(s);
+        S->events.push_back(e);
+        S->free_streams.push_back(i);
+    }
+    if (st == SELL_OK && cudaDeviceSynchronize() != cudaSuccess)
+        st = cuda_fail(cudaGetLastError(), "sell_server_create: arena");
+    if (st != SELL_OK) {
+        for (auto s : S->streams)
+            if (s) (void)cudaStreamDestroy(s);
+        for (auto e : S->events)
+            if (e) (void)cudaEventDestroy(e);
+        S->al.put(S->arena_base, nullptr);
+        delete S;
+        return st;
+    }
+    try {
+        S->thr = std::thread(scheduler, S);
+    } catch (...) {
+        for (auto s : S->streams) (void)cudaStreamDestroy(s);
+        for (auto e : S->events) (void)cudaEventDestroy(e);
+        S->al.put(S->arena_base, nullptr);
+        delete S;
+        return fail(SELL_ENOMEM, "sell_server_create: cannot start the scheduler thread");
+    }
+    *out = S;
+    return SELL_OK;
+}
+
+sell_status sell_server_submit(sell_server_t S, int32_t mid, const void *X, int32_t k, void *Y, uint32_t flags,
+                               uint64_t *id) {
+    if (!S || !id) return fail(SELL_EINVAL, "sell_server_submit: NULL argument");
+    if (mid < 0 || mid >= (int32_t)S->mats.size()) return fail(SELL_EINVAL, "sell_server_submit: bad matrix id");
+    if (k < 1) return fail(SELL_EINVAL, "sell_server_submit: need k >= 1");
+    if (flags & ~(SELL_SPMV_ACCUMULATE | SELL_SPMV_COMPENSATED))
+        return fail(SELL_EINVAL, "sell_server_submit: unsupported flags");
+    const sell_matrix *h = S->mats[mid];
+    if ((flags & SELL_SPMV_COMPENSATED) && h->store_type == SELL_F64)
+        return fail(SELL_EUNSUPPORTED, "compensated accumulation needs F32/BF16 storage");
+    if ((flags & SELL_SPMV_ACCUMULATE) && !Y)
+        return fail(SELL_EINVAL, "sell_server_submit: accumulating needs a host y");
+    if ((h->ncols > 0 && !X) || (X && !is_pinned_host(X)) || (Y && !is_pinned_host(Y)))
+        return fail(SELL_EINVAL, "sell_server_submit: X and Y must be page-locked host memory");
+    Req *r = new (std::nothrow) Req();
+    if (!r) return fail(SELL_ENOMEM, "sell_server_submit: host allocation failed");
+    r->mid = mid;
+    r->k = k;
+    r->flags = flags;
+    r->X = X;
+    r->Y = Y;
+    sizes(S, r);
+    if ((int64_t)footprint(r) > S->arena_bytes) {
+        delete r;
+        return fail(SELL_EINVAL, "sell_server_submit: the request alone exceeds the budget");
+    }
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        if (S->stop) {
+            delete r;
+            return fail(SELL_EINVAL, "sell_server_submit: the server is stopping");
+        }
+        r->id = S->next_id++;
+        r->ta = now_s();
+        S->reqs[r->id] = r;
+        S->queue.push_back(r);
+        S->nreq += 1;
+        *id = r->id;
+    }
+    S->cv_work.notify_one();
+    return SELL_OK;
+}
+
+sell_status sell_server_wait(sell_server_t S, uint64_t id, double timeout_s, sell_request_info *info) {
+    if (!S) return fail(SELL_EINVAL, "sell_server_wait: NULL server");
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(id);
+    if (it == S->reqs.end()) return fail(SELL_EINVAL, "sell_server_wait: unknown request");
+    Req *r = it->second;
+    const auto until = std::chrono::steady_clock::now() +
+                       std::chrono::duration_cast<std::chrono::steady_clock::duration>(
+                           std::chrono::duration<double>(timeout_s > 0 ? timeout_s : 0));
+    while (r->state != kDone) {
+        if (S->cv_done.wait_until(lk, until) == std::cv_status::timeout && r->state != kDone)
+            return fail(SELL_ETIMEOUT, "sell_server_wait: timed out");
+    }
+    if (info) {
+        info->t_arrive = r->ta;
+        info->t_launch = r->tl;
+        info->t_done = r->td;
+        info->batch = r->batch;
+        info->status = r->status;
+    }
+    const sell_status st = (sell_status)r->status;
+    if (!r->keep_y() || r->status != SELL_OK) {  // nothing left on the device: forget it
+        S->reqs.erase(it);
+        delete r;
+    }
+    if (st != SELL_OK) return fail(st, "sell_server_wait: the request's batch failed");
+    return SELL_OK;
+}
+
+sell_status sell_server_result(sell_server_t S, uint64_t id, void **dev_y) {
+    if (!S || !dev_y) return fail(SELL_EINVAL, "sell_server_result: NULL argument");
+    std::lock_guard<std::mutex> g(S->mu);
+    auto it = S->reqs.find(id);
+    if (it == S->reqs.end() || !it->second->keep_y() || it->second->state != kDone)
+        return fail(SELL_EINVAL, "sell_server_result: not a completed device-result request");
+    *dev_y = S->arena_base + it->second->yoff;
+    return SELL_OK;
+}
+
+sell_status sell_server_release(sell_server_t S, uint64_t id) {
+    if (!S) return fail(SELL_EINVAL, "sell_server_release: NULL server");
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        auto it = S->reqs.find(id);
+        if (it == S->reqs.end() || !it->second->keep_y() || it->second->state != kDone)
+            return fail(SELL_EINVAL, "sell_server_release: not a completed device-result request");
+        release_y(S, it->second);
+        delete it->second;
+        S->reqs.erase(it);
+    }
+    S->cv_work.notify_one();
+    return SELL_OK;
+}
+
+sell_status sell_server_stats(sell_server_t S, sell_server_stats_t *st) {
+    if (!S || !st) return fail(SELL_EINVAL, "sell_server_stats: NULL argument");
+    std::lock_guard<std::mutex> g(S->mu);
+    st->requests = S->nreq;
+    st->batches = S->nbatch;
+    st->batched_requests = S->nbatched;
+    st->queued = (int64_t)S->queue.size();
+    st->resident_bytes = S->resident;
+    st->budget_bytes = S->budget;
+    st->in_use_bytes = S->resident + S->used;
+    st->peak_bytes = S->resident + S->peak_used;
+    return SELL_OK;
+}
+
+sell_status sell_server_destroy(sell_server_t S) {
+    if (!S) return SELL_OK;
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        S->stop = true;
+    }
+    S->cv_work.notify_all();
+    if (S->thr.joinable()) S->thr.join();
+    for (auto s : S->streams) (void)cudaStreamSynchronize(s);
+    for (auto s : S->streams) (void)cudaStreamDestroy(s);
+    for (auto e : S->events) (void)cudaEventDestroy(e);
+    S->al.put(S->arena_base, nullptr);
+    (void)cudaDeviceSynchronize();
+    for (auto &kv : S->reqs) delete kv.second;
+    delete S;
+    return SELL_OK;
+}
+
+}  // extern "C"

@@ -61,6 +61,21 @@ class sell_batch_item(ctypes.Structure):
                 ("flags", ctypes.c_uint32)]
 
 
+class sell_server_opts(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_int64), ("max_batch", ctypes.c_int32), ("streams", ctypes.c_int32)]
+
+
+class sell_request_info(ctypes.Structure):
+    _fields_ = [("t_arrive", ctypes.c_double), ("t_launch", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("batch", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+
+class sell_server_stats_t(ctypes.Structure):
+    _fields_ = [("requests", ctypes.c_int64), ("batches", ctypes.c_int64), ("batched_requests", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("resident_bytes", ctypes.c_int64), ("budget_bytes", ctypes.c_int64),
+                ("in_use_bytes", ctypes.c_int64), ("peak_bytes", ctypes.c_int64)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -86,6 +101,15 @@ SIGNATURES = {
                                          ctypes.POINTER(_P)]),
     "sell_batch_run": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
     "sell_batch_free": (ctypes.c_int, [_P]),
+    "sell_server_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.POINTER(sell_server_opts),
+                                          ctypes.POINTER(_P)]),
+    "sell_server_submit": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32, _P, ctypes.c_uint32,
+                                          ctypes.POINTER(ctypes.c_uint64)]),
+    "sell_server_wait": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(sell_request_info)]),
+    "sell_server_result": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(_P)]),
+    "sell_server_release": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "sell_server_stats": (ctypes.c_int, [_P, ctypes.POINTER(sell_server_stats_t)]),
+    "sell_server_destroy": (ctypes.c_int, [_P]),
     "sell_bench_read": (ctypes.c_int, [_P, ctypes.c_size_t, _P, ctypes.c_int32, _P]),
     "sell_bench_fma64": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P]),
     "sell_bench_gather": (ctypes.c_int, [_P, ctypes.c_int64, _P, ctypes.c_int32, ctypes.c_int32, _P]),
@@ -374,3 +398,45 @@ def use_torch_allocator(enable: bool = True):
     a, f = ALLOC_FN(_alloc), FREE_FN(_free)
     _check(lib.sell_set_allocator(a, f, None))
     _alloc_keep = (a, f)
+
+
+# ------------------------------------------------------------------ serving
+def sell_server_create(mats, budget_bytes: int, max_batch: int = 64, streams: int = 3) -> int:
+    arr = (_P * len(mats))(*[m.handle.value for m in mats])
+    o = sell_server_opts(int(budget_bytes), int(max_batch), int(streams))
+    out = _P()
+    _check(load().sell_server_create(arr, len(mats), ctypes.byref(o), ctypes.byref(out)))
+    return out.value
+
+
+def sell_server_submit(srv: int, mid: int, X_ptr: int, k: int, Y_ptr: int | None, flags: int = 0) -> int:
+    rid = ctypes.c_uint64()
+    _check(load().sell_server_submit(_P(srv), int(mid), _P(X_ptr), int(k), _P(Y_ptr or 0), int(flags),
+                                     ctypes.byref(rid)))
+    return rid.value
+
+
+def sell_server_wait(srv: int, rid: int, timeout_s: float = 60.0) -> sell_request_info:
+    info = sell_request_info()
+    _check(load().sell_server_wait(_P(srv), ctypes.c_uint64(rid), float(timeout_s), ctypes.byref(info)))
+    return info
+
+
+def sell_server_result(srv: int, rid: int) -> int:
+    out = _P()
+    _check(load().sell_server_result(_P(srv), ctypes.c_uint64(rid), ctypes.byref(out)))
+    return out.value
+
+
+def sell_server_release(srv: int, rid: int):
+    _check(load().sell_server_release(_P(srv), ctypes.c_uint64(rid)))
+
+
+def sell_server_stats(srv: int) -> dict:
+    st = sell_server_stats_t()
+    _check(load().sell_server_stats(_P(srv), ctypes.byref(st)))
+    return {name: getattr(st, name) for name, _ in st._fields_}
+
+
+def sell_server_destroy(srv: int):
+    _check(load().sell_server_destroy(_P(srv)))

@@ -1,21 +1,22 @@
-"""Continuous-batching SpMV/SpMMV server over device-resident SELL-C-sigma
-matrices (an extension: the paper stops at single products).
+"""Python face of the native continuous-batching server (sell_server_* in
+include/sell.h; the scheduler, admission, batching and stream handling run in
+the C++ library).
 
-Requests (matrix id, block of right-hand sides in pinned host memory) arrive
-at any time.  A scheduler thread admits them in arrival order while their
-device buffers fit in the HBM budget next to the resident matrices, packs the
-admitted ones into one persistent batched launch (sell_batch_create /
-sell_batch_run), and keeps up to `streams` batches in flight at once: requests
-that arrive while others run on the GPU are admitted as soon as a stream and
-memory are free, and their work overlaps on the device.  Each result is
-bitwise the same as the request run alone (the per-row arithmetic does not
-depend on the batch).  Latency is measured from arrival to the moment the
-result is back in host memory (or, for requests whose result stays on the
-device, to the completion of the batch on the GPU).
+Requests (matrix id, block of right-hand sides in pinned host memory) are
+queued from any thread.  The library's scheduler thread admits them in arrival
+order while their device footprint (x block, y block, long-row scratch) fits
+in an arena of budget - resident bytes, packs the admitted ones into one
+batched launch on a free stream and keeps up to `streams` batches in flight,
+so requests that arrive while others run are admitted as soon as a stream and
+memory are free and their work overlaps on the device.  Each result is
+bitwise the same as the request run alone.  Latency is measured by the
+library from arrival to the moment the request's batch has completed on the
+GPU (results copied back into the request's pinned host buffer, or left on
+the device).
 """
 from __future__ import annotations
 
-import collections
+import queue as _queue
 import threading
 import time
 from dataclasses import dataclass, field
@@ -25,193 +26,190 @@ import numpy as np
 from . import sell
 
 
+class _DeviceArray:
+    """__cuda_array_interface__ view of a device result (no copy)."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
 @dataclass
 class Request:
+    server: "Server"
     rid: int
     mid: int
-    X: object                  # pinned host tensor, ncols x k (float64 for F64 matrices, else float32)
+    X: object                  # pinned host tensor, ncols (k = 1) or ncols x k
     k: int
-    t_arrive: float
+    to_host: bool
+    Y: object = None           # pinned host result (to_host), else set by result()
+    t_arrive: float = 0.0
     t_launch: float = 0.0
     t_done: float = 0.0
-    Y: object = None           # result: pinned host tensor, or device tensor (to_host=False)
-    done: threading.Event = field(default_factory=threading.Event)
-    nbytes: int = 0
-    to_host: bool = True
+    batch: int = 0
+    finished: bool = False
+    released: bool = False
+    _lock: threading.Lock = field(default_factory=threading.Lock)
 
     @property
     def latency(self) -> float:
         return self.t_done - self.t_arrive
 
+    def wait(self, timeout: float = 60.0) -> "Request":
+        """Block until the request has completed (raises on timeout or error)."""
+        with self._lock:
+            if not self.finished:
+                info = sell.sell_server_wait(self.server.handle, self.rid, timeout)
+                self.t_arrive, self.t_launch, self.t_done = info.t_arrive, info.t_launch, info.t_done
+                self.batch = info.batch
+                self.finished = True
+                self.server._record(self)
+        return self
+
+    def result(self):
+        """The device result (to_host=False) as a torch tensor view, valid until release()."""
+        import torch
+        self.wait()
+        if self.to_host:
+            return self.Y
+        ptr = sell.sell_server_result(self.server.handle, self.rid)
+        inf = self.server.mats[self.mid].info
+        shape = (inf.nrows,) if self.X.dim() == 1 else (inf.nrows, self.k)
+        typestr = "<f8" if inf.store_type == sell.SELL_F64 else "<f4"
+        return torch.as_tensor(_DeviceArray(ptr, shape, typestr), device="cuda")
+
+    def release(self):
+        """Return a device result's memory to the server."""
+        if not self.to_host and not self.released:
+            self.wait()
+            sell.sell_server_release(self.server.handle, self.rid)
+            self.released = True
+
 
 class Server:
-    """Scheduler over resident matrices `mats` (list of SellMatrix)."""
+    """Native server over resident matrices `mats` (list of SellMatrix)."""
 
-    def __init__(self, mats, hbm_budget_bytes: int, max_batch: int = 128, streams: int = 3,
-                 max_wait_s: float = 0.0):
-        import torch
-        self.torch = torch
+    def __init__(self, mats, hbm_budget_bytes: int, max_batch: int = 128, streams: int = 3):
         self.mats = list(mats)
         self.resident = sum(h.info.device_bytes for h in self.mats)
-        if self.resident > hbm_budget_bytes:
-            raise ValueError("resident matrices exceed the HBM budget")
-        self.budget = hbm_budget_bytes
-        self.max_batch = max_batch
-        self.max_wait_s = max_wait_s
-        self.inflight_bytes = 0
-        self.peak_bytes = self.resident
-        self.q = collections.deque()
-        self.cv = threading.Condition()
-        self.streams = [torch.cuda.Stream() for _ in range(streams)]
-        self.free_streams = collections.deque(range(streams))
-        self.upload = torch.cuda.Stream()  # kept idle: plan uploads never wait on compute
-        self.inflight = []
-        self.completed = []
-        self.batches = 0
-        self.batch_sizes = []
-        self._stop = False
-        self._rid = 0
-        self.thread = None
-        self.device = torch.cuda.current_device()
+        if self.resident >= hbm_budget_bytes:
+            raise ValueError("resident matrices fill the HBM budget")
+        self.budget = int(hbm_budget_bytes)
+        self.handle = sell.sell_server_create(self.mats, self.budget, max_batch, streams)
+        self._done = []
+        self._done_lock = threading.Lock()
 
-    # ------------------------------------------------------------ client side
+    # -------------------------------------------------------------- client
     def request_bytes(self, mid: int, k: int) -> int:
+        """The x and y blocks of a request (the library adds long-row scratch)."""
         inf = self.mats[mid].info
         es = 8 if inf.store_type == sell.SELL_F64 else 4
         return (inf.ncols + inf.nrows) * k * es
 
     def submit(self, mid: int, X, to_host: bool = True) -> Request:
         """Queue Y = A_mid X.  X is a pinned host tensor (ncols, or ncols x k);
-        the result comes back to pinned host memory, or stays on the device
-        (to_host=False) for a consumer that works there."""
+        the result comes back to a pinned host tensor (to_host), or stays on
+        the device until Request.release()."""
+        import torch
         k = 1 if X.dim() == 1 else int(X.shape[1])
-        with self.cv:
-            r = Request(self._rid, mid, X, k, time.perf_counter(), to_host=to_host)
-            r.nbytes = self.request_bytes(mid, k)
-            if self.resident + r.nbytes > self.budget:
-                raise ValueError("request larger than the HBM budget")
-            self._rid += 1
-            self.q.append(r)
-            self.cv.notify()
-        return r
+        Y = None
+        if to_host:
+            inf = self.mats[mid].info
+            shape = (inf.nrows,) if X.dim() == 1 else (inf.nrows, k)
+            Y = torch.empty(shape, dtype=X.dtype, pin_memory=True)
+        try:
+            rid = sell.sell_server_submit(self.handle, mid, X.data_ptr(), k, Y.data_ptr() if Y is not None else None)
+        except sell.SellError as e:
+            raise ValueError(str(e)) from e
+        return Request(self, rid, mid, X, k, to_host, Y=Y)
 
-    # ------------------------------------------------------------ scheduler
+    def _record(self, r: Request):
+        with self._done_lock:
+            self._done.append((r.t_arrive, r.t_launch, r.t_done, r.batch))
+
+    # ----------------------------------------------------------- lifecycle
     def start(self):
-        self.thread = threading.Thread(target=self._loop, daemon=True)
-        self.thread.start()
-        return self
+        return self  # the scheduler thread runs from creation on
 
     def stop(self):
-        with self.cv:
-            self._stop = True
-            self.cv.notify()
-        if self.thread:
-            self.thread.join()
+        if self.handle:
+            sell.sell_server_destroy(self.handle)
+            self.handle = None
 
-    def _take(self):
-        """Admit queued requests in arrival order while they fit."""
-        batch = []
-        with self.cv:
-            while self.q and len(batch) < self.max_batch:
-                r = self.q[0]
-                if self.resident + self.inflight_bytes + r.nbytes > self.budget:
-                    break
-                self.q.popleft()
-                self.inflight_bytes += r.nbytes
-                batch.append(r)
-            self.peak_bytes = max(self.peak_bytes, self.resident + self.inflight_bytes)
-        return batch
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass
 
-    def _launch(self, batch):
-        torch = self.torch
-        si = self.free_streams.popleft()
-        s = self.streams[si]
-        items, bufs = [], []
-        now = time.perf_counter()
-        with torch.cuda.stream(s):
-            for r in batch:
-                h = self.mats[r.mid]
-                Xd = r.X.to(device=self.device, non_blocking=True)
-                shape = (h.info.nrows,) if r.X.dim() == 1 else (h.info.nrows, r.k)
-                Yd = torch.empty(shape, dtype=r.X.dtype, device=self.device)
-                items.append((h, Xd, Yd, 0))
-                bufs.append((r, Xd, Yd))
-                r.t_launch = now
-        plan = sell.sell_batch_create(items, stream=self.upload)
-        plan.run(stream=s)
-        with torch.cuda.stream(s):
-            for r, Xd, Yd in bufs:
-                if r.to_host:
-                    r.Y = torch.empty(Yd.shape, dtype=Yd.dtype, pin_memory=True)
-                    r.Y.copy_(Yd, non_blocking=True)
-                else:
-                    r.Y = Yd
-            ev = torch.cuda.Event()
-            ev.record(s)
-        self.inflight.append((si, ev, bufs, plan))
-        self.batches += 1
-        self.batch_sizes.append(len(batch))
-
-    def _poll(self):
-        done_any = False
-        for entry in list(self.inflight):
-            si, ev, bufs, plan = entry
-            if not ev.query():
-                continue
-            t = time.perf_counter()
-            self.inflight.remove(entry)
-            plan.free()
-            freed = 0
-            for r, Xd, Yd in bufs:
-                r.t_done = t
-                freed += r.nbytes
-                r.done.set()
-                self.completed.append(r)
-            with self.cv:
-                self.inflight_bytes -= freed
-            self.free_streams.append(si)
-            done_any = True
-        return done_any
-
-    def _loop(self):
-        self.torch.cuda.set_device(self.device)
-        while True:
-            self._poll()
-            launched = False
-            if self.free_streams:
-                if self.max_wait_s and self.inflight:
-                    # optional small wait to gather more requests into one launch
-                    with self.cv:
-                        if len(self.q) < self.max_batch:
-                            self.cv.wait(timeout=self.max_wait_s)
-                batch = self._take()
-                if batch:
-                    self._launch(batch)
-                    launched = True
-            with self.cv:
-                if self._stop and not self.q and not self.inflight:
-                    return
-                if not launched and not self.inflight and not self.q:
-                    self.cv.wait(timeout=0.01)
-            if not launched and self.inflight:
-                time.sleep(2e-5)
-
-    # ------------------------------------------------------------ reporting
+    # ----------------------------------------------------------- reporting
     def stats(self):
-        lat = np.array([r.latency for r in self.completed]) if self.completed else np.zeros(1)
-        return {"requests": len(self.completed), "batches": self.batches,
-                "mean_batch": float(np.mean(self.batch_sizes)) if self.batch_sizes else 0.0,
-                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-                "mean_ms": float(lat.mean() * 1e3), "peak_hbm_bytes": int(self.peak_bytes),
-                "budget_bytes": int(self.budget)}
+        st = sell.sell_server_stats(self.handle) if self.handle else {}
+        with self._done_lock:
+            d = np.array(self._done) if self._done else np.zeros((1, 4))
+        lat = d[:, 2] - d[:, 0]
+        out = {"requests": int(st.get("requests", len(self._done))), "batches": int(st.get("batches", 0)),
+               "mean_batch": float(st["batched_requests"] / max(1, st["batches"])) if st else 0.0,
+               "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+               "mean_ms": float(lat.mean() * 1e3), "peak_hbm_bytes": int(st.get("peak_bytes", 0)),
+               "budget_bytes": self.budget}
+        return out
+
+
+class _Consumer:
+    """A client thread that waits for requests in submission order and
+    releases device results at once (it uses each result as it arrives)."""
+
+    def __init__(self):
+        self.q = _queue.Queue()
+        self.errors = []
+        self.th = threading.Thread(target=self._run, daemon=True)
+        self.th.start()
+
+    def _run(self):
+        while True:
+            r = self.q.get()
+            if r is None:
+                return
+            try:
+                r.wait(120)
+                r.release()
+            except Exception as e:  # surfaced by finish()
+                self.errors.append(e)
+
+    def put(self, r):
+        self.q.put(r)
+
+    def finish(self):
+        self.q.put(None)
+        self.th.join()
+        if self.errors:
+            raise self.errors[0]
+
+
+def burst_load(server: Server, n: int, make_request, seed: int = 0, to_host: bool = True):
+    """Submit n requests at once; returns (requests, seconds until the last
+    completed)."""
+    rng = np.random.default_rng(seed)
+    c = _Consumer()
+    t0 = time.perf_counter()
+    reqs = []
+    for _ in range(n):
+        r = server.submit(*make_request(rng), to_host=to_host)
+        reqs.append(r)
+        c.put(r)
+    c.finish()
+    return reqs, time.perf_counter() - t0
 
 
 def poisson_load(server: Server, rate_hz: float, duration_s: float, make_request, seed: int = 0,
                  to_host: bool = True):
     """Submit requests with exponential inter-arrival times for duration_s;
-    make_request(rng) -> (mid, pinned X).  Returns the submitted requests."""
+    make_request(rng) -> (mid, pinned X); a consumer thread takes the
+    results as they arrive.  Returns the requests, all complete."""
     rng = np.random.default_rng(seed)
     reqs = []
+    c = _Consumer()
     t0 = time.perf_counter()
     t_next = t0
     while True:
@@ -224,5 +222,8 @@ def poisson_load(server: Server, rate_hz: float, duration_s: float, make_request
                 break
             time.sleep(min(t_next - now, 1e-4))
         mid, X = make_request(rng)
-        reqs.append(server.submit(mid, X, to_host=to_host))
+        r = server.submit(mid, X, to_host=to_host)
+        reqs.append(r)
+        c.put(r)
+    c.finish()
     return reqs

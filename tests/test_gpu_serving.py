@@ -61,50 +61,110 @@ def test_results_alone_equal_in_the_mix():
             mid, X = _make(mats, rng)
             reqs.append(srv.submit(mid, X, to_host=bool(rng.random() < 0.7)))
         time.sleep(0.002)
+    got = []
     for r in reqs:
-        assert r.done.wait(60)
-    srv.stop()
+        r.wait(60)
+        got.append(r.result().cpu().clone())
+        r.release()
     st = srv.stats()
+    srv.stop()
     assert st["requests"] == len(reqs) and st["batches"] >= 2
-    for r in reqs:
+    for r, y in zip(reqs, got):
         ref = _alone(mats[r.mid], r.X)
-        got = r.Y.cpu() if r.Y.is_cuda else r.Y
-        assert got.numpy().tobytes() == ref.numpy().tobytes(), f"request {r.rid} differs"
+        assert y.numpy().tobytes() == ref.numpy().tobytes(), f"request {r.rid} differs"
+
+
+def test_requests_arriving_during_a_batch_share_the_next_launch():
+    """With one stream, requests queued while a long product runs are admitted
+    together into the next launch, and every result still equals the request
+    alone."""
+    import torch
+    from paper_1307_6209_gb300 import serving, sell
+    big = sell.sell_build(synth.lognormal_device(2_000_000, seed=5), C=32, sigma=2_000_000)
+    mats = _mats(seed=40) + [big]
+    srv = serving.Server(mats, hbm_budget_bytes=sum(m.info.device_bytes for m in mats) + (4 << 30),
+                         max_batch=64, streams=1)
+    Xb = torch.rand((big.info.ncols, 8), dtype=torch.float64).pin_memory()
+    rng = np.random.default_rng(6)
+    made = [_make(mats[:-1], rng) for _ in range(10)]  # inputs ready before the first submit
+    first = srv.submit(len(mats) - 1, Xb, to_host=False)
+    rest = [srv.submit(mid, X, to_host=True) for mid, X in made]
+    for r in [first] + rest:
+        r.wait(60)
+    first.release()
+    srv.stop()
+    assert max(r.batch for r in rest) > 1, "queued requests did not share a launch"
+    assert all(r.t_launch >= first.t_launch for r in rest)
+    for r in rest:
+        assert r.Y.numpy().tobytes() == _alone(mats[r.mid], r.X).numpy().tobytes()
 
 
 def test_budget_is_respected_and_everything_completes():
     from paper_1307_6209_gb300 import serving
     mats = _mats(seed=10)
     resident = sum(h.info.device_bytes for h in mats)
-    srv_probe = serving.Server(mats, hbm_budget_bytes=resident + (1 << 30))
-    biggest = max(srv_probe.request_bytes(i, 8) for i in range(len(mats)))
-    budget = resident + biggest  # room for about one large request at a time
+    biggest = max((mats[i].info.ncols + mats[i].info.nrows) * 8 * 8 for i in range(len(mats)))
+    budget = resident + 2 * biggest  # room for about one large request at a time (plus scratch)
     srv = serving.Server(mats, hbm_budget_bytes=budget, max_batch=64, streams=3).start()
     rng = np.random.default_rng(2)
     reqs = [srv.submit(*_make(mats, rng)) for _ in range(60)]
     for r in reqs:
-        assert r.done.wait(60)
-    srv.stop()
+        r.wait(60)
     st = srv.stats()
+    srv.stop()
     assert st["peak_hbm_bytes"] <= budget
     assert st["requests"] == 60
     with pytest.raises(ValueError):
-        serving.Server(mats, hbm_budget_bytes=resident - 1)
-    small = serving.Server(mats, hbm_budget_bytes=resident + 16)
+        serving.Server(mats, hbm_budget_bytes=resident)
+    small = serving.Server(mats, hbm_budget_bytes=resident + 4096)
     import torch
     with pytest.raises(ValueError):
-        small.submit(1, torch.zeros(mats[1].info.ncols, dtype=torch.float32))
+        small.submit(1, torch.zeros(mats[1].info.ncols, dtype=torch.float32).pin_memory())
+    with pytest.raises(ValueError):  # pageable host memory is refused
+        small.submit(0, torch.zeros(4, dtype=torch.float64))
+    small.stop()
 
 
 def test_poisson_load_reports_latency():
     from paper_1307_6209_gb300 import serving
     mats = _mats(seed=20)
     srv = serving.Server(mats, hbm_budget_bytes=8 << 30, streams=3).start()
-    reqs = serving.poisson_load(srv, rate_hz=2000.0, duration_s=0.3, make_request=lambda g: _make(mats, g))
-    for r in reqs:
-        assert r.done.wait(60)
-    srv.stop()
+    reqs = serving.poisson_load(srv, rate_hz=2000.0, duration_s=0.3, make_request=lambda g: _make(mats, g),
+                                to_host=False)
     st = srv.stats()
+    srv.stop()
     assert st["requests"] == len(reqs) > 100
     assert 0 < st["p50_ms"] <= st["p99_ms"]
     assert all(r.t_arrive <= r.t_launch <= r.t_done for r in reqs)
+
+
+def test_native_accumulate_and_errors():
+    """Y += A X through the C entry points with a host y; unknown ids and
+    waits that time out are reported, not hung on."""
+    import torch
+    from paper_1307_6209_gb300 import sell
+    mats = _mats(seed=30)
+    h = mats[2]
+    srv = sell.sell_server_create(mats, sum(m.info.device_bytes for m in mats) + (1 << 30), 8, 2)
+    try:
+        x = torch.from_numpy(synth.vector(h.info.ncols, seed=3)).pin_memory()
+        y0 = synth.vector(h.info.nrows, seed=4)
+        y = torch.from_numpy(y0.copy()).pin_memory()
+        rid = sell.sell_server_submit(srv, 2, x.data_ptr(), 1, y.data_ptr(), sell.SELL_SPMV_ACCUMULATE)
+        info = sell.sell_server_wait(srv, rid, 60.0)
+        assert info.status == sell.SELL_OK and info.t_done >= info.t_launch >= info.t_arrive
+        yd = torch.from_numpy(y0.copy()).cuda()
+        sell.sell_spmv(h, x.cuda(), yd, flags=sell.SELL_SPMV_ACCUMULATE)
+        torch.cuda.synchronize()
+        assert y.numpy().tobytes() == yd.cpu().numpy().tobytes()
+        with pytest.raises(sell.SellError) as e:
+            sell.sell_server_wait(srv, rid, 1.0)  # a host-result request is forgotten after its wait
+        assert e.value.status == sell.SELL_EINVAL
+        with pytest.raises(sell.SellError) as e:  # accumulating needs a host y
+            sell.sell_server_submit(srv, 2, x.data_ptr(), 1, None, sell.SELL_SPMV_ACCUMULATE)
+        assert e.value.status == sell.SELL_EINVAL
+        with pytest.raises(sell.SellError) as e:
+            sell.sell_server_submit(srv, 0, x.data_ptr(), 1, None, sell.SELL_SPMV_COMPENSATED)
+        assert e.value.status == sell.SELL_EUNSUPPORTED
+    finally:
+        sell.sell_server_destroy(srv)
