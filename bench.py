@@ -739,10 +739,17 @@ def run_ours(args):
         del csr_d
         torch.cuda.empty_cache()
         if not args.no_extras and args.workload == "lognormal" and rank == 0:
-            extras["stencil27"] = stencil_section(sell, model, stream, peak, fma_tf)
-            extras["pathological"] = pathological_section(sell, model, stream, peak)
-            extras["batched"] = batched_section(sell, autotune, stream)
-            extras["serving"] = serving_section(sell, stream)
+            # each extra section reports its own failure instead of losing the line
+            for key, fn in (("stencil27", lambda: stencil_section(sell, model, stream, peak, fma_tf)),
+                            ("pathological", lambda: pathological_section(sell, model, stream, peak)),
+                            ("batched", lambda: batched_section(sell, autotune, stream)),
+                            ("serving", lambda: serving_section(sell, stream))):
+                try:
+                    extras[key] = fn()
+                except Exception as e:  # noqa: BLE001 -- recorded in the JSON line
+                    extras[key] = {"error": f"{type(e).__name__}: {e}"}
+                    torch.cuda.synchronize()
+                    torch.cuda.empty_cache()
 
     # ---- roofline of the dominant kernel (the SpMV)
     alg = model.algorithmic_bytes(A.nrows, A.ncols, A.nnz, inf.nchunks, C, 8, 8, inf.has_perm)

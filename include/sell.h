@@ -348,6 +348,11 @@ SELL_API sell_status sell_server_submit(sell_server_t srv, int32_t mid, const vo
  * Errors: SELL_EINVAL (unknown id), SELL_ETIMEOUT, the batch's error. */
 SELL_API sell_status sell_server_wait(sell_server_t srv, uint64_t id, double timeout_s, sell_request_info *info);
 
+/* Deliver the next completed request not yet delivered by a wait, in
+ * completion order: *id and *info (may be NULL), with the same forgetting
+ * rule as sell_server_wait.  Blocks up to timeout_s (SELL_ETIMEOUT). */
+SELL_API sell_status sell_server_next(sell_server_t srv, double timeout_s, uint64_t *id, sell_request_info *info);
+
 /* Device address of a completed device-result request's Y (nrows x k). */
 SELL_API sell_status sell_server_result(sell_server_t srv, uint64_t id, void **dev_y);
 
@@ -358,7 +363,8 @@ SELL_API sell_status sell_server_release(sell_server_t srv, uint64_t id);
 SELL_API sell_status sell_server_stats(sell_server_t srv, sell_server_stats_t *stats);
 
 /* Finish every queued and running request, stop the scheduler and free the
- * server (NULL accepted). */
+ * server (NULL accepted).  Device results not yet released are dropped first
+ * (their memory goes with the server). */
 SELL_API sell_status sell_server_destroy(sell_server_t srv);
 
 /* ------------------------------------------------------------ measuring */

@@ -97,6 +97,7 @@ struct Req {
     double ta = 0, tl = 0, td = 0;
     int state = kQueued;
     int32_t status = SELL_OK, batch = 0;
+    bool collected = false;  // delivered by sell_server_wait or sell_server_next
     bool keep_y() const { return Y == nullptr; }
 };
 
@@ -134,6 +135,7 @@ struct sell_server {
     std::condition_variable cv_work, cv_done;
     std::deque<sell::Req *> queue;
     std::unordered_map<uint64_t, sell::Req *> reqs;
+    std::deque<uint64_t> completed;  // in completion order, for sell_server_next
     uint64_t next_id = 1;
     int64_t nreq = 0, nbatch = 0, nbatched = 0;
     bool stop = false;
@@ -261,6 +263,7 @@ void scheduler(sell_server *S) {
                 release_x_s(S, r);
                 if (!r->keep_y() || r->status != SELL_OK) release_y(S, r);
                 r->state = kDone;
+                S->completed.push_back(r->id);
             }
             if (B.plan) {
                 batch_release(B.plan, S->streams[B.si]);
@@ -301,6 +304,33 @@ void scheduler(sell_server *S) {
         else
             S->cv_work.wait_for(lk, std::chrono::microseconds(20));  // poll the events
     }
+}
+
+}  // namespace
+}  // namespace sell
+
+namespace sell {
+namespace {
+
+// Deliver a completed request (lock held): fill *info; a request with nothing
+// left on the device is forgotten, a device result stays until its release.
+sell_status collect(sell_server *S, std::unordered_map<uint64_t, Req *>::iterator it, sell_request_info *info) {
+    Req *r = it->second;
+    if (info) {
+        info->t_arrive = r->ta;
+        info->t_launch = r->tl;
+        info->t_done = r->td;
+        info->batch = r->batch;
+        info->status = r->status;
+    }
+    r->collected = true;
+    const sell_status st = (sell_status)r->status;
+    if (!r->keep_y() || r->status != SELL_OK) {
+        S->reqs.erase(it);
+        delete r;
+    }
+    if (st != SELL_OK) return fail(st, "sell_server: the request's batch failed");
+    return SELL_OK;
 }
 
 }  // namespace
@@ -437,20 +467,27 @@ sell_status sell_server_wait(sell_server_t S, uint64_t id, double timeout_s, sel
         if (S->cv_done.wait_until(lk, until) == std::cv_status::timeout && r->state != kDone)
             return fail(SELL_ETIMEOUT, "sell_server_wait: timed out");
     }
-    if (info) {
-        info->t_arrive = r->ta;
-        info->t_launch = r->tl;
-        info->t_done = r->td;
-        info->batch = r->batch;
-        info->status = r->status;
+    return collect(S, it, info);
+}
+
+sell_status sell_server_next(sell_server_t S, double timeout_s, uint64_t *id, sell_request_info *info) {
+    if (!S || !id) return fail(SELL_EINVAL, "sell_server_next: NULL argument");
+    std::unique_lock<std::mutex> lk(S->mu);
+    const auto until = std::chrono::steady_clock::now() +
+                       std::chrono::duration_cast<std::chrono::steady_clock::duration>(
+                           std::chrono::duration<double>(timeout_s > 0 ? timeout_s : 0));
+    for (;;) {
+        while (!S->completed.empty()) {
+            const uint64_t rid = S->completed.front();
+            S->completed.pop_front();
+            auto it = S->reqs.find(rid);
+            if (it == S->reqs.end() || it->second->collected) continue;  // collected by a wait
+            *id = rid;
+            return collect(S, it, info);
+        }
+        if (S->cv_done.wait_until(lk, until) == std::cv_status::timeout && S->completed.empty())
+            return fail(SELL_ETIMEOUT, "sell_server_next: no request completed in time");
     }
-    const sell_status st = (sell_status)r->status;
-    if (!r->keep_y() || r->status != SELL_OK) {  // nothing left on the device: forget it
-        S->reqs.erase(it);
-        delete r;
-    }
-    if (st != SELL_OK) return fail(st, "sell_server_wait: the request's batch failed");
-    return SELL_OK;
 }
 
 sell_status sell_server_result(sell_server_t S, uint64_t id, void **dev_y) {
@@ -495,8 +532,20 @@ sell_status sell_server_stats(sell_server_t S, sell_server_stats_t *st) {
 sell_status sell_server_destroy(sell_server_t S) {
     if (!S) return SELL_OK;
     {
+        // results still held on the device die with the server; returning
+        // them first lets every queued request be admitted and finish
         std::lock_guard<std::mutex> g(S->mu);
         S->stop = true;
+        for (auto it = S->reqs.begin(); it != S->reqs.end();) {
+            Req *r = it->second;
+            if (r->state == kDone && r->keep_y() && r->reserved) {
+                release_y(S, r);
+                delete r;
+                it = S->reqs.erase(it);
+            } else {
+                ++it;
+            }
+        }
     }
     S->cv_work.notify_all();
     if (S->thr.joinable()) S->thr.join();

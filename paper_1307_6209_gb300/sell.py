@@ -106,6 +106,8 @@ SIGNATURES = {
     "sell_server_submit": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32, _P, ctypes.c_uint32,
                                           ctypes.POINTER(ctypes.c_uint64)]),
     "sell_server_wait": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(sell_request_info)]),
+    "sell_server_next": (ctypes.c_int, [_P, ctypes.c_double, ctypes.POINTER(ctypes.c_uint64),
+                                        ctypes.POINTER(sell_request_info)]),
     "sell_server_result": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(_P)]),
     "sell_server_release": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "sell_server_stats": (ctypes.c_int, [_P, ctypes.POINTER(sell_server_stats_t)]),
@@ -420,6 +422,14 @@ def sell_server_wait(srv: int, rid: int, timeout_s: float = 60.0) -> sell_reques
     info = sell_request_info()
     _check(load().sell_server_wait(_P(srv), ctypes.c_uint64(rid), float(timeout_s), ctypes.byref(info)))
     return info
+
+
+def sell_server_next(srv: int, timeout_s: float = 60.0):
+    """(id, info) of the next completed request, in completion order."""
+    rid = ctypes.c_uint64()
+    info = sell_request_info()
+    _check(load().sell_server_next(_P(srv), float(timeout_s), ctypes.byref(rid), ctypes.byref(info)))
+    return rid.value, info
 
 
 def sell_server_result(srv: int, rid: int) -> int:

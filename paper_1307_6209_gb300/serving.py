@@ -16,7 +16,6 @@ the device).
 """
 from __future__ import annotations
 
-import queue as _queue
 import threading
 import time
 from dataclasses import dataclass, field
@@ -98,6 +97,7 @@ class Server:
         self.handle = sell.sell_server_create(self.mats, self.budget, max_batch, streams)
         self._done = []
         self._done_lock = threading.Lock()
+        self._pending = {}  # id -> Request, until collected
 
     # -------------------------------------------------------------- client
     def request_bytes(self, mid: int, k: int) -> int:
@@ -117,15 +117,35 @@ class Server:
             inf = self.mats[mid].info
             shape = (inf.nrows,) if X.dim() == 1 else (inf.nrows, k)
             Y = torch.empty(shape, dtype=X.dtype, pin_memory=True)
-        try:
-            rid = sell.sell_server_submit(self.handle, mid, X.data_ptr(), k, Y.data_ptr() if Y is not None else None)
-        except sell.SellError as e:
-            raise ValueError(str(e)) from e
-        return Request(self, rid, mid, X, k, to_host, Y=Y)
+        # registered under the lock that next() takes to look a request up, so
+        # a request that completes at once is never delivered unknown
+        with self._done_lock:
+            try:
+                rid = sell.sell_server_submit(self.handle, mid, X.data_ptr(), k,
+                                              Y.data_ptr() if Y is not None else None)
+            except sell.SellError as e:
+                raise ValueError(str(e)) from e
+            r = Request(self, rid, mid, X, k, to_host, Y=Y)
+            self._pending[rid] = r
+        return r
+
+    def next(self, timeout: float = 60.0) -> Request:
+        """The next completed request, in completion order (raises SellError
+        with SELL_ETIMEOUT when none completes in time)."""
+        rid, info = sell.sell_server_next(self.handle, timeout)
+        with self._done_lock:
+            r = self._pending.get(rid)
+        with r._lock:
+            r.t_arrive, r.t_launch, r.t_done = info.t_arrive, info.t_launch, info.t_done
+            r.batch = info.batch
+            r.finished = True
+        self._record(r)
+        return r
 
     def _record(self, r: Request):
         with self._done_lock:
             self._done.append((r.t_arrive, r.t_launch, r.t_done, r.batch))
+            self._pending.pop(r.rid, None)
 
     # ----------------------------------------------------------- lifecycle
     def start(self):
@@ -157,31 +177,46 @@ class Server:
 
 
 class _Consumer:
-    """A client thread that waits for requests in submission order and
-    releases device results at once (it uses each result as it arrives)."""
+    """A client thread that takes requests as they complete (completion
+    order, sell_server_next) and releases device results at once."""
 
-    def __init__(self):
-        self.q = _queue.Queue()
+    def __init__(self, server: Server):
+        self.server = server
+        self.submitted = 0
+        self.collected = 0
+        self.closed = False
         self.errors = []
         self.th = threading.Thread(target=self._run, daemon=True)
         self.th.start()
 
     def _run(self):
-        while True:
-            r = self.q.get()
-            if r is None:
-                return
+        last = time.perf_counter()
+        while not (self.closed and self.collected >= self.submitted):
             try:
-                r.wait(120)
-                r.release()
+                r = self.server.next(0.05)
+                last = time.perf_counter()
+            except sell.SellError as e:
+                if e.status == sell.SELL_ETIMEOUT:
+                    if self.collected < self.submitted and time.perf_counter() - last > 120.0:
+                        self.errors.append(TimeoutError("no request completed for 120 s"))
+                        return
+                    continue
+                self.errors.append(e)
+                return
             except Exception as e:  # surfaced by finish()
                 self.errors.append(e)
+                return
+            try:
+                r.release()
+            except Exception as e:
+                self.errors.append(e)
+            self.collected += 1
 
     def put(self, r):
-        self.q.put(r)
+        self.submitted += 1
 
     def finish(self):
-        self.q.put(None)
+        self.closed = True
         self.th.join()
         if self.errors:
             raise self.errors[0]
@@ -191,7 +226,7 @@ def burst_load(server: Server, n: int, make_request, seed: int = 0, to_host: boo
     """Submit n requests at once; returns (requests, seconds until the last
     completed)."""
     rng = np.random.default_rng(seed)
-    c = _Consumer()
+    c = _Consumer(server)
     t0 = time.perf_counter()
     reqs = []
     for _ in range(n):
@@ -209,7 +244,7 @@ def poisson_load(server: Server, rate_hz: float, duration_s: float, make_request
     results as they arrive.  Returns the requests, all complete."""
     rng = np.random.default_rng(seed)
     reqs = []
-    c = _Consumer()
+    c = _Consumer(server)
     t0 = time.perf_counter()
     t_next = t0
     while True:

@@ -160,6 +160,19 @@ def test_native_accumulate_and_errors():
         with pytest.raises(sell.SellError) as e:
             sell.sell_server_wait(srv, rid, 1.0)  # a host-result request is forgotten after its wait
         assert e.value.status == sell.SELL_EINVAL
+        # completion-order delivery: two device results, each delivered once
+        x1 = torch.ones(mats[1].info.ncols, dtype=torch.float32).pin_memory()
+        x3 = torch.ones(mats[3].info.ncols, dtype=torch.float32).pin_memory()
+        r1 = sell.sell_server_submit(srv, 1, x1.data_ptr(), 1, None)
+        r2 = sell.sell_server_submit(srv, 3, x3.data_ptr(), 1, None)
+        got = {sell.sell_server_next(srv, 60.0)[0], sell.sell_server_next(srv, 60.0)[0]}
+        assert got == {r1, r2}
+        with pytest.raises(sell.SellError) as e:
+            sell.sell_server_next(srv, 0.05)
+        assert e.value.status == sell.SELL_ETIMEOUT
+        for r in (r1, r2):
+            assert sell.sell_server_result(srv, r)
+            sell.sell_server_release(srv, r)
         with pytest.raises(sell.SellError) as e:  # accumulating needs a host y
             sell.sell_server_submit(srv, 2, x.data_ptr(), 1, None, sell.SELL_SPMV_ACCUMULATE)
         assert e.value.status == sell.SELL_EINVAL
