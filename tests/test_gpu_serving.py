@@ -181,3 +181,30 @@ def test_native_accumulate_and_errors():
         assert e.value.status == sell.SELL_EUNSUPPORTED
     finally:
         sell.sell_server_destroy(srv)
+
+
+def test_destroy_with_unreleased_results_does_not_wait_forever():
+    """A device result that is never released blocks a queued request that
+    needs its memory; destroying the server drops the held result, lets the
+    queued request finish and returns."""
+    import torch
+    from paper_1307_6209_gb300 import sell
+    n = 50000
+    h = sell.sell_build(synth.lognormal_device(n, seed=60, cap=64), C=32, sigma=n, store_type=sell.SELL_F32)
+    # no long rows, so a k = 2 request needs exactly its x and y blocks: 16 n
+    # bytes; the arena holds one request (20 n), and a second one only once
+    # the first result's 8 n bytes are released
+    srv = sell.sell_server_create([h], h.info.device_bytes + 20 * n, 4, 2)
+    x = torch.ones((n, 2), dtype=torch.float32).pin_memory()
+    held = sell.sell_server_submit(srv, 0, x.data_ptr(), 2, None)
+    sell.sell_server_wait(srv, held, 60.0)
+    blocked = sell.sell_server_submit(srv, 0, x.data_ptr(), 2, None)
+    time.sleep(0.2)
+    st = sell.sell_server_stats(srv)
+    assert st["queued"] == 1  # waits for the held result's memory
+    done = threading.Event()
+    t = threading.Thread(target=lambda: (sell.sell_server_destroy(srv), done.set()), daemon=True)
+    t.start()
+    t.join(60)
+    assert done.is_set(), "sell_server_destroy did not return"
+    assert blocked
