@@ -171,6 +171,17 @@ SELL_API sell_status sell_build(const sell_csr *A, const sell_opts *opts, void *
  * on F64 storage), SELL_ENOMEM (HOST_IO staging), SELL_ECUDA. */
 SELL_API sell_status sell_spmv(sell_handle h, const void *x, void *y, uint32_t flags, void *stream);
 
+/* y = A x (as sell_spmv, same flags but SELL_SPMV_HOST_IO) followed by
+ * *dot = x . y in binary64 (a Krylov step's p . Ap; not in the paper, which
+ * names other kernels over SELL-C-sigma as open work).  A must be square; x
+ * and y are in the same order (original, or sorted with
+ * SELL_BUILD_PERMUTE_COLS).  The dot is summed in a fixed order over the
+ * vector (1024 contiguous ranges, fixed trees), so its bits depend only on x
+ * and y, not on the format, the launch or the run.  dot is a device pointer.
+ * Errors: those of sell_spmv, SELL_EINVAL (NULL dot, non-square A, HOST_IO). */
+SELL_API sell_status sell_spmv_dot(sell_handle h, const void *x, void *y, uint32_t flags, double *dot,
+                                   void *stream);
+
 /* Y = A X for k right-hand sides (not in the paper; the matrix is streamed
  * once for up to 8 vectors).  X is ncols x k and Y nrows x k, row-major with
  * leading dimensions ldx >= k and ldy >= k (in elements); element types as in

@@ -119,7 +119,7 @@ void free_matrix(sell_matrix *h) {
     (void)cudaDeviceSynchronize();
     void *ptrs[] = {h->val,    h->col,   h->cs,   h->cl,     h->srl,    h->perm,
                     h->lchunk, h->lunit, h->cnt, h->cnt2, h->part, h->io[0].x, h->io[0].y,
-                    h->io[1].x, h->io[1].y, h->bsc, h->wsplit, h->dstat};
+                    h->io[1].x, h->io[1].y, h->bsc, h->wsplit, h->dstat, h->dot_part};
     for (void *p : ptrs) h->al.put(p, nullptr);
     for (auto &sl : h->io)
         if (sl.done) (void)cudaEventDestroy(sl.done);
@@ -226,6 +226,19 @@ sell_status sell_spmmv(sell_handle h, const void *X, int64_t ldx, void *Y, int64
 
 sell_status sell_spmv(sell_handle h, const void *x, void *y, uint32_t flags, void *stream) {
     return sell_spmmv(h, x, 1, y, 1, 1, flags, stream);
+}
+
+sell_status sell_spmv_dot(sell_handle h, const void *x, void *y, uint32_t flags, double *dot, void *stream) {
+    if (!h || !dot) return fail(SELL_EINVAL, "sell_spmv_dot: NULL argument");
+    if (h->nrows != h->ncols) return fail(SELL_EINVAL, "sell_spmv_dot: the matrix must be square");
+    if (flags & SELL_SPMV_HOST_IO) return fail(SELL_EINVAL, "sell_spmv_dot: device vectors only");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    SELL_TRY(sell_spmmv(h, x, 1, y, 1, 1, flags, stream));
+    if (h->nrows == 0) {
+        SELL_CUDA_TRY(cudaMemsetAsync(dot, 0, sizeof(double), s));
+        return SELL_OK;
+    }
+    return launch_dot(h, x, y, dot, s);
 }
 
 sell_status sell_set_launch(sell_handle h, int32_t block, int32_t unroll, int32_t pipeline) {

@@ -90,6 +90,7 @@ struct sell_matrix {
     int64_t wsplit_n = 0;
     int32_t *dstat = nullptr;  // device status word: 1 after a bounded wait gave up
     int32_t bulk_grid = 0, bulk_warps = 0, bulk_ring = 0;
+    double *dot_part = nullptr;  // range sums of sell_spmv_dot (lazily allocated)
     // host-io staging (lazily allocated): two slots used in turn, so that the
     // copies of one call overlap the kernel of the previous one when calls
     // alternate streams.  done = recorded after the slot's last device-to-host
@@ -135,6 +136,7 @@ sell_status launch_block_with_scratch(const sell_matrix *h, const void *X, int64
 sell_status build_format(const sell_csr *A, const sell_opts *o, cudaStream_t s, sell_matrix *h);
 sell_status bulk_plan(sell_matrix *h, int64_t nwarps, cudaStream_t s);
 sell_status bulk_prepare(sell_matrix *h);
+sell_status launch_dot(sell_matrix *h, const void *x, const void *y, double *out, cudaStream_t s);
 // scratch: per item, batch_item_scratch() bytes of device memory (or NULL for
 // items without long rows); NULL: the plan allocates its own.
 sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s, sell_batch *b,

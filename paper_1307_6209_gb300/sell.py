@@ -88,6 +88,7 @@ SIGNATURES = {
     "sell_spmv": (ctypes.c_int, [_P, _P, _P, ctypes.c_uint32, _P]),
     "sell_spmmv": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32,
                                   ctypes.c_uint32, _P]),
+    "sell_spmv_dot": (ctypes.c_int, [_P, _P, _P, ctypes.c_uint32, _P, _P]),
     "sell_spmmv_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32,
                                           ctypes.c_uint32, _P]),
     "sell_set_launch": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
@@ -243,6 +244,12 @@ def sell_build(A, C: int = 32, sigma: int = 1, store_type: int = SELL_F64, flags
 def sell_spmv(h: SellMatrix, x, y, flags: int = 0, stream=None):
     _check(load().sell_spmv(h.handle, _ptr(x), _ptr(y), int(flags), _stream_ptr(stream)))
     return y
+
+
+def sell_spmv_dot(h: SellMatrix, x, y, dot, flags: int = 0, stream=None):
+    """y = A x, then dot[0] = x . y (binary64, fixed summation order); dot is a
+    device float64 tensor of at least one element."""
+    _check(load().sell_spmv_dot(h.handle, _ptr(x), _ptr(y), int(flags), _ptr(dot), _stream_ptr(stream)))
 
 
 def sell_spmmv(h: SellMatrix, X, Y, flags: int = 0, stream=None, ldx=None, ldy=None, k=None):
