@@ -119,7 +119,8 @@ void free_matrix(sell_matrix *h) {
     (void)cudaDeviceSynchronize();
     void *ptrs[] = {h->val,    h->col,   h->cs,   h->cl,     h->srl,    h->perm,
                     h->lchunk, h->lunit, h->cnt, h->cnt2, h->part, h->io[0].x, h->io[0].y,
-                    h->io[1].x, h->io[1].y, h->bsc, h->wsplit, h->dstat, h->dot_part};
+                    h->io[1].x, h->io[1].y, h->bsc, h->wsplit, h->dstat, h->dot_part,
+                    h->lrow,   h->lmeta};
     for (void *p : ptrs) h->al.put(p, nullptr);
     for (auto &sl : h->io)
         if (sl.done) (void)cudaEventDestroy(sl.done);

@@ -37,6 +37,8 @@ struct Prod {
     const int32_t *perm;
     const int32_t *lchunk;
     const int2 *lunit;
+    const int4 *lmeta;
+    const int32_t *lrow;
     void *part;    // this product's own segment scratch (owned by the plan)
     int32_t *cnt;  // this product's own segment counters (owned by the plan)
     int32_t *cnt2; // this product's own group counters (owned by the plan)
@@ -53,7 +55,7 @@ struct Prod {
 // start[i+1]); ranges 0..nprod-1 are the products' long-row units
 // (kTileRows segment threads per block), ranges nprod..2*nprod-1 their short
 // rows (kTileRows rows per block).
-constexpr int kLaunchProds = 160;  // 160 * 152 B + the ranges fit the 32 KB parameter limit
+constexpr int kLaunchProds = 160;  // 160 * 168 B + the ranges fit the 32 KB parameter limit
 
 struct LaunchParams {
     Prod prods[kLaunchProds];
@@ -84,7 +86,7 @@ k_batch(const __grid_constant__ LaunchParams lp) {
         const int64_t v = first + threadIdx.x;
         if (v < P.long_threads)
             long_unit<VT, XT, K, U, false, Acc>(static_cast<const VT *>(P.val), P.col, P.cs, P.srl, P.perm, P.lchunk,
-                                         P.lunit, static_cast<Acc *>(P.part), P.cnt, P.cnt2,
+                                         P.lunit, P.lmeta, P.lrow, static_cast<Acc *>(P.part), P.cnt, P.cnt2,
                                          static_cast<const XT *>(P.X),
                                          P.ldx, static_cast<XT *>(P.Y), P.ldy, P.N, P.C, v, P.acc, P.vec != 0, pol);
         return;
@@ -190,6 +192,8 @@ sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s
             P.srl = h->srl;
             P.lchunk = h->lchunk;
             P.lunit = h->lunit;
+            P.lmeta = h->lmeta;
+            P.lrow = h->lrow;
             P.part = nullptr;
             P.cnt = nullptr;
             P.cnt2 = nullptr;

@@ -349,6 +349,30 @@ __global__ void k_long_units(const int32_t *__restrict__ nseg, const int64_t *__
         for (int32_t sg = 0; sg < nseg[i]; ++sg) lunit[ubase[i] + sg] = make_int2((int)i, sg);
 }
 
+// Long rows of each long chunk: lrow[i*C + k] = the lane of its k-th row
+// longer than kSeg (lane order), lmeta[i] = {m rows, mode, units of the
+// chunk, 0}.  Mode 0: unit thread t takes lane t (its row's segment); mode 1,
+// for chunks whose long rows are few (8 m <= C): the chunk's unit threads
+// take consecutive segments of one long row after another, so a warp runs 32
+// segments of a long row instead of one segment of each of 32 mostly short
+// rows.  Either way each segment is the same chain and lands in the same
+// partial slot (unit of the segment, lane of the row), so the results do not
+// depend on the mode.
+__global__ void k_long_rows(const int32_t *__restrict__ srl, int64_t N, int C, const int32_t *__restrict__ lchunk,
+                            const int32_t *__restrict__ nseg, int64_t nlong, int32_t *__restrict__ lrow,
+                            int4 *__restrict__ lmeta) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nlong; i += stride) {
+        const int64_t c = lchunk[i];
+        int m = 0;
+        for (int l = 0; l < C; ++l) {
+            const int64_t r = c * C + l;
+            if (r < N && srl[r] > kSeg) lrow[i * C + m++] = l;
+        }
+        lmeta[i] = make_int4(m, 8 * m <= C ? 1 : 0, nseg[i], 0);
+    }
+}
+
 // ------------------------------------------------- bulk-staged SpMV plan
 // bsc[c] = the longest row of at most kSeg entries in chunk c, -1 if the
 // chunk has no such row (the columns of chunk c that the bulk-staged SpMV
@@ -651,7 +675,7 @@ sell_status build_format(const sell_csr *A, const sell_opts *o, cudaStream_t s, 
         SELL_CUDA_TRY(cudaMemcpyAsync(&nlong, lpos.as<int64_t>() + Nc, sizeof(int64_t),
                                       cudaMemcpyDeviceToHost, s));
     SELL_CUDA_TRY(cudaStreamSynchronize(s));
-    DevBuf lchunk, lnseg, lubase, lunit, cnt, cnt2, part;
+    DevBuf lchunk, lnseg, lubase, lunit, cnt, cnt2, part, lrow, lmeta;
     int64_t nunits = 0;
     if (nlong > 0) {
         SELL_TRY(lchunk.alloc(al, nlong * sizeof(int32_t), s));
@@ -670,6 +694,12 @@ sell_status build_format(const sell_csr *A, const sell_opts *o, cudaStream_t s, 
         SELL_TRY(lunit.alloc(al, nunits * sizeof(int2), s));
         k_long_units<<<grid_for(nlong, 256), 256, 0, s>>>(lnseg.as<int32_t>(), lubase.as<int64_t>(), nlong,
                                                           lunit.as<int2>());
+        SELL_CUDA_TRY(cudaGetLastError());
+        SELL_TRY(lrow.alloc(al, (size_t)nlong * C * sizeof(int32_t), s));
+        SELL_TRY(lmeta.alloc(al, (size_t)nlong * sizeof(int4), s));
+        k_long_rows<<<grid_for(nlong, 256), 256, 0, s>>>(srl.as<int32_t>(), N, C, lchunk.as<int32_t>(),
+                                                         lnseg.as<int32_t>(), nlong, lrow.as<int32_t>(),
+                                                         lmeta.as<int4>());
         SELL_CUDA_TRY(cudaGetLastError());
         SELL_TRY(cnt.alloc(al, nlong * C * sizeof(int32_t), s));
         SELL_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, nlong * C * sizeof(int32_t), s));
@@ -721,9 +751,11 @@ sell_status build_format(const sell_csr *A, const sell_opts *o, cudaStream_t s, 
     h->nunits = nunits;
     h->part_k = nunits > 0 ? 1 : 0;
     h->device_bytes = val.bytes + col.bytes + cs.bytes + cl.bytes + srl.bytes + perm.bytes + lchunk.bytes +
-                      lunit.bytes + cnt.bytes + cnt2.bytes + part.bytes;
+                      lunit.bytes + cnt.bytes + cnt2.bytes + part.bytes + lrow.bytes + lmeta.bytes;
     h->lchunk = (int32_t *)lchunk.release_ownership();
     h->lunit = (int2 *)lunit.release_ownership();
+    h->lrow = (int32_t *)lrow.release_ownership();
+    h->lmeta = (int4 *)lmeta.release_ownership();
     h->cnt = (int32_t *)cnt.release_ownership();
     h->cnt2 = (int32_t *)cnt2.release_ownership();
     h->part = part.release_ownership();

@@ -79,6 +79,8 @@ struct sell_matrix {
     int32_t *lchunk = nullptr; // nlong chunks holding rows longer than kSeg
     int64_t nlong = 0;
     int2 *lunit = nullptr;     // nunits long-row work units {long chunk, segment}
+    int32_t *lrow = nullptr;   // nlong * C lanes of each long chunk's long rows
+    int4 *lmeta = nullptr;     // nlong {long rows, mode, units, 0} (sell_build.cu k_long_rows)
     int64_t nunits = 0;
     int32_t *cnt = nullptr;    // nlong * C per-row segment counters (zero at rest)
     int32_t *cnt2 = nullptr;   // nunits * C group counters of very long rows (zero at rest)

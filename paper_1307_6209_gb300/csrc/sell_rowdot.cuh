@@ -265,21 +265,34 @@ template <class VT, class XT, int K, int U, bool PIPE, class Acc>
 __device__ __forceinline__ void long_unit(const VT *__restrict__ val, const int32_t *__restrict__ col,
                                           const int64_t *__restrict__ cs, const int32_t *__restrict__ srl,
                                           const int32_t *__restrict__ perm, const int32_t *__restrict__ lchunk,
-                                          const int2 *__restrict__ lunit, Acc *part, int32_t *cnt, int32_t *cnt2,
-                                          const XT *__restrict__ X, int64_t ldx, XT *Y, int64_t ldy,
-                                          int64_t N, int C, int64_t v, int accumulate, bool vec,
+                                          const int2 *__restrict__ lunit, const int4 *__restrict__ lmeta,
+                                          const int32_t *__restrict__ lrow, Acc *part, int32_t *cnt,
+                                          int32_t *cnt2, const XT *__restrict__ X, int64_t ldx, XT *Y,
+                                          int64_t ldy, int64_t N, int C, int64_t v, int accumulate, bool vec,
                                           uint64_t pol) {
     const int64_t u = v / C;
-    const int l = (int)(v - u * C);
+    const int t = (int)(v - u * C);
     const int2 us = lunit[u];
+    const int4 meta = lmeta[us.x];
+    int l, s;
+    if (meta.y == 0) {  // thread t takes lane t
+        l = t;
+        s = us.y;
+    } else {  // the chunk's threads take consecutive segments of each long row
+        const int i = us.y * C + t;
+        const int k = i / meta.z;
+        if (k >= meta.x) return;
+        s = i - k * meta.z;
+        l = lrow[(int64_t)us.x * C + k];
+    }
     const int64_t c = lchunk[us.x];
     const int64_t r = c * C + l;
     if (r >= N) return;
     const int L = srl[r];
     if (L <= kSeg) return;  // short rows belong to the per-row path
     const int nseg = (L + kSeg - 1) / kSeg;
-    const int s = us.y;
     if (s >= nseg) return;
+    const int64_t u0 = u - us.y;  // the chunk's first unit; segment s's partial sits in unit u0 + s
     const int64_t out = perm ? (int64_t)perm[r] : r;
     Acc acc[K];
 #pragma unroll
@@ -288,8 +301,7 @@ __device__ __forceinline__ void long_unit(const VT *__restrict__ val, const int3
     chain<VT, XT, K, U, PIPE, Acc>(acc, val + base, col + base, C, s * kSeg, min(L, (s + 1) * kSeg), X, ldx,
                                    vec, pol);
 #pragma unroll
-    for (int q = 0; q < K; ++q) part[(u * C + l) * K + q] = acc[q];
-    const int64_t u0 = u - s;
+    for (int q = 0; q < K; ++q) part[((u0 + s) * C + l) * K + q] = acc[q];
     int32_t *ct = cnt + (int64_t)us.x * C + l;
     Acc tot[K];
     if (nseg <= kSuper) {

@@ -124,6 +124,8 @@ struct Args {
     const int32_t *wsplit;   // nwarps + 1 chunk boundaries
     const int32_t *lchunk;
     const int2 *lunit;
+    const int4 *lmeta;
+    const int32_t *lrow;
     Acc *part;
     int32_t *cnt, *cnt2;
     int32_t *dstat;
@@ -220,9 +222,9 @@ __global__ void __launch_bounds__(512) k_spmv_bulk(const __grid_constant__ Args<
     // ---- long-row work units first (their copies above are already in flight)
     if constexpr (LONG) {
         for (int64_t v = wg * 32 + lane; v < a.long_threads; v += NW * 32)
-            long_unit<VT, XT, 1, 4, false, Acc>(a.val, a.col, a.cs, a.srl, a.perm, a.lchunk, a.lunit, a.part,
-                                                a.cnt, a.cnt2, a.X, a.ldx, a.Y, a.ldy, a.N, C, v, a.accumulate,
-                                                false, pol);
+            long_unit<VT, XT, 1, 4, false, Acc>(a.val, a.col, a.cs, a.srl, a.perm, a.lchunk, a.lunit, a.lmeta,
+                                                a.lrow, a.part, a.cnt, a.cnt2, a.X, a.ldx, a.Y, a.ldy, a.N, C, v,
+                                                a.accumulate, false, pol);
         __syncwarp();
     }
 
@@ -338,6 +340,8 @@ cudaError_t run(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64
     a.wsplit = h->wsplit;
     a.lchunk = h->lchunk;
     a.lunit = h->lunit;
+    a.lmeta = h->lmeta;
+    a.lrow = h->lrow;
     a.part = static_cast<Acc *>(h->part);
     a.cnt = h->cnt;
     a.cnt2 = h->cnt2;

@@ -31,7 +31,8 @@ template <class VT, int K, int U, bool PIPE, class Acc, bool LONG>
 __global__ void __launch_bounds__(512)
 k_spmmv(const VT *__restrict__ val, const int32_t *__restrict__ col, const int64_t *__restrict__ cs,
         const int32_t *__restrict__ srl, const int32_t *__restrict__ perm, const int32_t *__restrict__ lchunk,
-        const int2 *__restrict__ lunit, int64_t long_threads, int64_t long_blocks, Acc *part, int32_t *cnt,
+        const int2 *__restrict__ lunit, const int4 *__restrict__ lmeta, const int32_t *__restrict__ lrow,
+        int64_t long_threads, int64_t long_blocks, Acc *part, int32_t *cnt,
         int32_t *cnt2,
         const typename XType<VT>::T *__restrict__ X, int64_t ldx, typename XType<VT>::T *Y, int64_t ldy,
         int64_t N, int C, int accumulate, int vec) {
@@ -41,8 +42,8 @@ k_spmmv(const VT *__restrict__ val, const int32_t *__restrict__ col, const int64
         if (blockIdx.x < long_blocks) {
             const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
             if (v < long_threads)
-                long_unit<VT, XT, K, U, PIPE, Acc>(val, col, cs, srl, perm, lchunk, lunit, part, cnt, cnt2, X, ldx, Y,
-                                             ldy, N, C, v, accumulate, vec != 0, pol);
+                long_unit<VT, XT, K, U, PIPE, Acc>(val, col, cs, srl, perm, lchunk, lunit, lmeta, lrow, part, cnt,
+                                                   cnt2, X, ldx, Y, ldy, N, C, v, accumulate, vec != 0, pol);
             return;
         }
     }
@@ -63,7 +64,8 @@ cudaError_t run(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64
     auto kern = h->nunits ? k_spmmv<VT, K, U, PIPE, Acc, true> : k_spmmv<VT, K, U, PIPE, Acc, false>;
     kern<<<(unsigned)grid, h->block, 0, s>>>(
         static_cast<const VT *>(h->val), h->col, h->cs, h->srl,
-        (h->flags & SELL_BUILD_PERMUTE_COLS) ? nullptr : h->perm, h->lchunk, h->lunit, long_threads,
+        (h->flags & SELL_BUILD_PERMUTE_COLS) ? nullptr : h->perm, h->lchunk, h->lunit, h->lmeta, h->lrow,
+        long_threads,
         long_blocks, static_cast<Acc *>(h->part), h->cnt, h->cnt2, static_cast<const XT *>(X), ldx,
         static_cast<XT *>(Y), ldy, h->nrows, h->C, acc, vec);
     return cudaGetLastError();
@@ -80,7 +82,8 @@ cudaError_t run_with(const sell_matrix *h, const void *X, int64_t ldx, void *Y, 
     auto kern = h->nunits ? k_spmmv<VT, K, U, PIPE, Acc, true> : k_spmmv<VT, K, U, PIPE, Acc, false>;
     kern<<<(unsigned)grid, h->block, 0, s>>>(
         static_cast<const VT *>(h->val), h->col, h->cs, h->srl,
-        (h->flags & SELL_BUILD_PERMUTE_COLS) ? nullptr : h->perm, h->lchunk, h->lunit, long_threads,
+        (h->flags & SELL_BUILD_PERMUTE_COLS) ? nullptr : h->perm, h->lchunk, h->lunit, h->lmeta, h->lrow,
+        long_threads,
         long_blocks, static_cast<Acc *>(part), cnt, cnt2, static_cast<const XT *>(X), ldx, static_cast<XT *>(Y),
         ldy, h->nrows, h->C, acc, vec);
     return cudaGetLastError();

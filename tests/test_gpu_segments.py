@@ -47,14 +47,22 @@ def _row_result(vals, xs, y0):
     return fold([fold(parts[g:g + SUPER]) for g in range(0, len(parts), SUPER)])
 
 
-def _matrix():
+def _matrix(spread=False):
+    """The special lengths in the first 64 rows, or (spread) one every 40 rows,
+    so that a chunk of up to 32 rows holds at most one long row -- the long
+    rows then run segment by segment across the chunk's threads."""
     lens = [0, 1, 5, 63, 64, 65, 100, 127, 128, 129, 192, 200, 257, 640, 1000, 3, 1500, 2000, 1089, 4096,
             4100, 9000, 16384, 16385, 20000, 33000]
     rng = np.random.default_rng(42)
     n = 40000
     rows = []
-    for i in range(300):
-        L = lens[i % len(lens)] if i < 64 else int(rng.integers(0, 40))
+    nrows = 64 * 40 if spread else 300
+    for i in range(nrows):
+        if spread:
+            special = i % 40 == 0
+            L = lens[(i // 40) % len(lens)] if special else int(rng.integers(0, 40))
+        else:
+            L = lens[i % len(lens)] if i < 64 else int(rng.integers(0, 40))
         rows.append(np.sort(rng.choice(n, size=L, replace=False)))
     rl = np.array([len(r) for r in rows])
     col = np.concatenate(rows).astype(np.int32)
@@ -64,12 +72,13 @@ def _matrix():
     return synth.CSR(len(rows), n, rpt, col, val)
 
 
+@pytest.mark.parametrize("spread", [False, True])
 @pytest.mark.parametrize("accumulate", [False, True])
-def test_f64_rows_match_documented_arithmetic(accumulate):
+def test_f64_rows_match_documented_arithmetic(accumulate, spread):
     import torch
     from paper_1307_6209_gb300 import sell
 
-    A = _matrix()
+    A = _matrix(spread)
     x = synth.vector(A.ncols, seed=9)
     y0 = synth.vector(A.nrows, seed=10)
     expect = np.array([
