@@ -26,6 +26,13 @@
  *     / cudaFreeAsync) from one library-owned memory pool per device, which
  *     keeps freed memory for reuse; sell_free returns the pool's unused
  *     memory to the device.
+ *   - Concurrency: a handle's products share its long-row scratch, so
+ *     products of one handle must not overlap on the GPU (issue them on one
+ *     stream, or order the streams), except that SELL_SPMV_HOST_IO products
+ *     are ordered by the library, and sell_spmmv_noalloc / batch plans use
+ *     scratch of their own.  Calls that change a handle (sell_set_launch,
+ *     sell_free) must not race with other calls on it from other host
+ *     threads.  A server (sell_server_*) may be used from any thread.
  */
 #ifndef SELL_H
 #define SELL_H
