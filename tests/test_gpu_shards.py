@@ -1,0 +1,51 @@
+"""Row sharding of one matrix, run shard after shard on one GPU.
+
+dist.shard_rows cuts the rows at multiples of lcm(min(sigma, N), C), so no
+sorting window and no chunk crosses a shard: each shard's GPU format must be
+exactly the matching piece of the global format, and with the full x (what
+one allgather gives every rank) the shards' y slices must concatenate to the
+global y bit for bit."""
+import numpy as np
+import pytest
+
+from paper_1307_6209_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _slice(A, r0, r1):
+    return synth.CSR(r1 - r0, A.ncols, A.rpt[r0:r1 + 1] - A.rpt[r0], A.col[A.rpt[r0]:A.rpt[r1]],
+                     A.val[A.rpt[r0]:A.rpt[r1]])
+
+
+@pytest.mark.parametrize("world", [2, 3, 5])
+@pytest.mark.parametrize("C,sigma", [(32, 256), (64, 1), (128, 4096)])
+def test_shards_are_pieces_and_concatenate_bitwise(world, C, sigma):
+    import torch
+    from paper_1307_6209_gb300 import dist as sdist
+    from paper_1307_6209_gb300 import sell
+
+    A = synth.lognormal(30011, seed=7, cap=900)
+    x = torch.from_numpy(synth.vector(A.ncols, seed=8)).cuda()
+    hg = sell.sell_build(A, C=C, sigma=sigma)
+    G = sell.sell_export(hg)
+    yg = torch.empty(A.nrows, dtype=torch.float64, device="cuda")
+    sell.sell_spmv(hg, x, yg)
+    parts = []
+    for r0, r1 in sdist.shard_rows(A.nrows, sigma, C, world, rpt=A.rpt):
+        S = _slice(A, r0, r1)
+        hs = sell.sell_build(S, C=C, sigma=sigma)
+        F = sell.sell_export(hs)
+        c0, c1 = r0 // C, r0 // C + hs.info.nchunks
+        assert np.array_equal(F["cs"], G["cs"][c0:c1 + 1] - G["cs"][c0])
+        assert F["val"].tobytes() == G["val"][G["cs"][c0]:G["cs"][c1]].tobytes()
+        assert np.array_equal(F["col"], G["col"][G["cs"][c0]:G["cs"][c1]])
+        if sigma > 1:
+            assert np.array_equal(F["perm"] + r0, G["perm"][r0:r1])
+        ys = torch.empty(r1 - r0, dtype=torch.float64, device="cuda")
+        sell.sell_spmv(hs, x, ys)
+        parts.append(ys)
+        hs.free()
+    torch.cuda.synchronize()
+    assert torch.cat(parts).cpu().numpy().tobytes() == yg.cpu().numpy().tobytes()
+    hg.free()
