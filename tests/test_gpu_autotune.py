@@ -1,0 +1,58 @@
+"""The autotuner and the profiling tool: the tuner measures every candidate,
+returns one of them, caches it by matrix signature, and the tuned handle
+gives the same bits as any other format (the choice is a speed choice only)."""
+import json
+
+import numpy as np
+import pytest
+
+from paper_1307_6209_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def test_tune_candidates_cache_and_invariance(tmp_path):
+    import torch
+    from paper_1307_6209_gb300 import autotune, sell
+
+    A = synth.lognormal(20000, seed=11, cap=600)
+    cache = str(tmp_path / "tune.json")
+    kw = dict(Cs=(32, 64), sigmas=(1, 4096), blocks=(128, 256), unrolls=(1, 4), pipelines=(0, 1, 2), keep=2,
+              reps=3, cache=cache)
+    r = autotune.tune(A, **kw)
+    assert not r.cached
+    assert {(f["C"], f["sigma"]) for f in r.formats} == {(32, 1), (32, 4096), (64, 1), (64, 4096)}
+    best = r.best
+    assert (best.C, best.sigma) in {(f["C"], f["sigma"]) for f in r.formats}
+    assert best.block in (128, 256) and best.unroll in (1, 4) and best.pipeline in (0, 1, 2)
+    assert min(l["us"] for l in r.launches) == pytest.approx(best.us)
+    # the second call is answered from the cache
+    r2 = autotune.tune(A, **kw)
+    assert r2.cached and (r2.best.C, r2.best.sigma, r2.best.block) == (best.C, best.sigma, best.block)
+    assert json.load(open(cache))
+    # the tuned handle computes the same bits as a plain SELL-32-1 handle
+    h = autotune.build_tuned(A, best)
+    h0 = sell.sell_build(A, C=32, sigma=1)
+    x = torch.from_numpy(synth.vector(A.ncols, seed=1)).cuda()
+    y, y0 = (torch.empty(A.nrows, dtype=torch.float64, device="cuda") for _ in range(2))
+    sell.sell_spmv(h, x, y)
+    sell.sell_spmv(h0, x, y0)
+    torch.cuda.synchronize()
+    assert y.cpu().numpy().tobytes() == y0.cpu().numpy().tobytes()
+
+
+def test_tune_batch_picks_a_candidate():
+    from paper_1307_6209_gb300 import autotune
+    samples = [synth.banded(3000 + 500 * i, seed=i) for i in range(4)] + \
+              [synth.lognormal(4000 + 300 * i, seed=10 + i, cap=300) for i in range(4)]
+    best, table = autotune.tune_batch(samples, Cs=(32, 64), sigmas=(1, 256), reps=3)
+    assert len(table) == 4 and all(t["us"] > 0 for t in table)
+    assert best["us"] == min(t["us"] for t in table)
+
+
+def test_profile_case_runs(capsys):
+    from paper_1307_6209_gb300 import profile_case
+    assert profile_case.main(["--matrix", "stencil27", "--n", "24", "--store", "bf16", "--pipeline", "1",
+                              "--unroll", "8", "--reps", "2"]) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["nnz"] == (3 * 24 - 2) ** 3 and line["us"] > 0 and line["store"] == "bf16"
