@@ -52,9 +52,11 @@ k_spmmv(const VT *__restrict__ val, const int32_t *__restrict__ col, const int64
     short_row<VT, XT, K, U, PIPE, Acc>(val, col, cs, srl, perm, X, ldx, Y, ldy, C, r, accumulate, vec != 0, pol);
 }
 
+// One launch of k_spmmv with the given long-row scratch (the handle's own,
+// or the caller's for sell_spmmv_noalloc).
 template <class VT, int K, int U, bool PIPE, class Acc>
-cudaError_t run(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy, int acc,
-                int vec, cudaStream_t s) {
+cudaError_t run_with(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy, int acc,
+                     int vec, void *part, int32_t *cnt, int32_t *cnt2, cudaStream_t s) {
     using XT = typename XType<VT>::T;
     const int64_t long_threads = h->nunits * h->C;
     const int64_t long_blocks = (long_threads + h->block - 1) / h->block;
@@ -65,28 +67,15 @@ cudaError_t run(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64
     kern<<<(unsigned)grid, h->block, 0, s>>>(
         static_cast<const VT *>(h->val), h->col, h->cs, h->srl,
         (h->flags & SELL_BUILD_PERMUTE_COLS) ? nullptr : h->perm, h->lchunk, h->lunit, h->lmeta, h->lrow,
-        long_threads,
-        long_blocks, static_cast<Acc *>(h->part), h->cnt, h->cnt2, static_cast<const XT *>(X), ldx,
+        long_threads, long_blocks, static_cast<Acc *>(part), cnt, cnt2, static_cast<const XT *>(X), ldx,
         static_cast<XT *>(Y), ldy, h->nrows, h->C, acc, vec);
     return cudaGetLastError();
 }
 
-// Same launch with caller-chosen segment scratch (used by sell_spmmv_noalloc).
 template <class VT, int K, int U, bool PIPE, class Acc>
-cudaError_t run_with(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy, int acc,
-                     int vec, void *part, int32_t *cnt, int32_t *cnt2, cudaStream_t s) {
-    using XT = typename XType<VT>::T;
-    const int64_t long_threads = h->nunits * h->C;
-    const int64_t long_blocks = (long_threads + h->block - 1) / h->block;
-    const int64_t grid = long_blocks + (h->nrows + h->block - 1) / h->block;
-    auto kern = h->nunits ? k_spmmv<VT, K, U, PIPE, Acc, true> : k_spmmv<VT, K, U, PIPE, Acc, false>;
-    kern<<<(unsigned)grid, h->block, 0, s>>>(
-        static_cast<const VT *>(h->val), h->col, h->cs, h->srl,
-        (h->flags & SELL_BUILD_PERMUTE_COLS) ? nullptr : h->perm, h->lchunk, h->lunit, h->lmeta, h->lrow,
-        long_threads,
-        long_blocks, static_cast<Acc *>(part), cnt, cnt2, static_cast<const XT *>(X), ldx, static_cast<XT *>(Y),
-        ldy, h->nrows, h->C, acc, vec);
-    return cudaGetLastError();
+cudaError_t run(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy, int acc,
+                int vec, cudaStream_t s) {
+    return run_with<VT, K, U, PIPE, Acc>(h, X, ldx, Y, ldy, acc, vec, h->part, h->cnt, h->cnt2, s);
 }
 
 template <class VT, class Acc>
