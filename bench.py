@@ -547,10 +547,10 @@ def serving_section(sell, stream, nmat=64, seed=0, duration_s=1.5):
         return mid, (buf[:n] if k == 1 else buf[:n * k].view(n, k))
 
     # warm-up (kernels, arena, pinned memory), then the saturated rate from a burst
-    srv = serving.Server(mats, budget, max_batch=64, streams=3)
+    srv = serving.Server(mats, budget, max_batch=64, streams=6)
     serving.burst_load(srv, 200, make, seed=1, to_host=False)
     srv.stop()
-    srv = serving.Server(mats, budget, max_batch=64, streams=3)
+    srv = serving.Server(mats, budget, max_batch=64, streams=6)
     burst, dt = serving.burst_load(srv, 400, make, seed=2, to_host=False)
     sat = len(burst) / dt
     out = {"workload": f"{nmat} resident matrices, rows log-uniform [10k, 4M], lognormal rows, half FP64 / "
@@ -562,7 +562,7 @@ def serving_section(sell, stream, nmat=64, seed=0, duration_s=1.5):
            "saturated_req_per_s": round(sat, 1), "burst": srv.stats()}
     srv.stop()
     for frac in (0.5, 0.8, 0.95):
-        srv = serving.Server(mats, budget, max_batch=64, streams=3)
+        srv = serving.Server(mats, budget, max_batch=64, streams=6)
         reqs = serving.poisson_load(srv, rate_hz=frac * sat, duration_s=duration_s, make_request=make, seed=7,
                                     to_host=False)
         t_end = max(r.t_done for r in reqs)

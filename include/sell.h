@@ -329,6 +329,10 @@ typedef struct {
     int64_t budget_bytes; /* device bytes for the resident handles plus all requests in flight */
     int32_t max_batch;    /* requests per batch, 1..4096 */
     int32_t streams;      /* batches in flight, 1..16 */
+    int32_t size_ratio;   /* 0 or 1: a batch takes queued requests in arrival order; r > 1: a batch takes
+                             the oldest request, then later ones whose work (stored elements x k) is
+                             within a factor r of it, so small requests do not wait for a large one */
+    int32_t reserved;     /* 0 */
 } sell_server_opts;
 
 typedef struct {

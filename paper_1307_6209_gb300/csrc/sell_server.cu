@@ -123,7 +123,7 @@ struct sell_server {
     std::vector<sell_matrix *> mats;
     int device = 0;
     int64_t budget = 0, resident = 0, arena_bytes = 0, used = 0, peak_used = 0;
-    int32_t max_batch = 64, nstreams = 3;
+    int32_t max_batch = 64, nstreams = 3, size_ratio = 0;
     sell::Allocator al;
     char *arena_base = nullptr;
     sell::Arena arena;
@@ -153,6 +153,9 @@ void sizes(const sell_server *S, Req *r) {
     r->yb = (size_t)h->nrows * r->k * es;
     r->sb = batch_item_scratch(h, r->k, nullptr);
 }
+
+// Work of a request: stored elements times right-hand sides.
+double work(const sell_server *S, const Req *r) { return (double)S->mats[r->mid]->stored * r->k; }
 
 size_t footprint(const Req *r) { return region(r->xb) + region(r->yb) + (r->sb ? round256(r->sb) : 0); }
 
@@ -274,15 +277,43 @@ void scheduler(sell_server *S) {
             retired = true;
         }
         if (retired) S->cv_done.notify_all();
-        // admit in arrival order while the footprint fits, then launch
+        // admit in arrival order while the footprint fits, then launch.  With
+        // a size ratio, the batch takes the oldest request and then, among the
+        // next requests in order, those whose work is within the ratio of it
+        // (the others wait for the next batch, on another stream), so small
+        // requests do not wait for the end of a large one's launch.
         if (!S->free_streams.empty() && !S->queue.empty()) {
             std::vector<Req *> batch;
-            while (!S->queue.empty() && (int)batch.size() < S->max_batch) {
-                Req *r = S->queue.front();
-                if (!reserve(S, r)) break;
-                S->queue.pop_front();
-                r->state = kRunning;
-                batch.push_back(r);
+            if (S->size_ratio <= 1) {
+                while (!S->queue.empty() && (int)batch.size() < S->max_batch) {
+                    Req *r = S->queue.front();
+                    if (!reserve(S, r)) break;
+                    S->queue.pop_front();
+                    r->state = kRunning;
+                    batch.push_back(r);
+                }
+            } else {
+                Req *head = S->queue.front();
+                if (reserve(S, head)) {
+                    S->queue.pop_front();
+                    head->state = kRunning;
+                    batch.push_back(head);
+                    const double w0 = work(S, head), q = (double)S->size_ratio;
+                    size_t scan = std::min(S->queue.size(), (size_t)4 * S->max_batch);
+                    for (size_t i = 0; i < scan && (int)batch.size() < S->max_batch;) {
+                        Req *r = S->queue[i];
+                        const double w = work(S, r);
+                        if (w > w0 * q || w * q < w0) {
+                            ++i;
+                            continue;
+                        }
+                        if (!reserve(S, r)) break;
+                        S->queue.erase(S->queue.begin() + (std::ptrdiff_t)i);
+                        --scan;
+                        r->state = kRunning;
+                        batch.push_back(r);
+                    }
+                }
             }
             if (!batch.empty()) {
                 const int si = S->free_streams.front();
@@ -342,8 +373,9 @@ extern "C" {
 
 sell_status sell_server_create(const sell_handle *mats, int32_t n, const sell_server_opts *o, sell_server_t *out) {
     if (!mats || n < 1 || !o || !out) return fail(SELL_EINVAL, "sell_server_create: bad arguments");
-    if (o->max_batch < 1 || o->max_batch > 4096 || o->streams < 1 || o->streams > 16)
-        return fail(SELL_EINVAL, "sell_server_create: need 1 <= max_batch <= 4096 and 1 <= streams <= 16");
+    if (o->max_batch < 1 || o->max_batch > 4096 || o->streams < 1 || o->streams > 16 || o->size_ratio < 0)
+        return fail(SELL_EINVAL,
+                    "sell_server_create: need 1 <= max_batch <= 4096, 1 <= streams <= 16, size_ratio >= 0");
     sell_server *S = new (std::nothrow) sell_server();
     if (!S) return fail(SELL_ENOMEM, "sell_server_create: host allocation failed");
     int dev = 0;
@@ -369,6 +401,7 @@ sell_status sell_server_create(const sell_handle *mats, int32_t n, const sell_se
     S->arena_bytes = (S->budget - S->resident) / 256 * 256;
     S->max_batch = o->max_batch;
     S->nstreams = o->streams;
+    S->size_ratio = o->size_ratio;
     S->al = current_allocator();
     S->arena_base = static_cast<char *>(S->al.get((size_t)S->arena_bytes, nullptr));
     if (!S->arena_base) {

@@ -208,3 +208,20 @@ def test_destroy_with_unreleased_results_does_not_wait_forever():
     t.join(60)
     assert done.is_set(), "sell_server_destroy did not return"
     assert blocked
+
+
+def test_size_ratio_batches_keep_results_and_order():
+    """With a size ratio the oldest request still goes first and every result
+    is the request alone; batches then hold requests of similar work."""
+    from paper_1307_6209_gb300 import serving
+    mats = _mats(seed=70)
+    srv = serving.Server(mats, hbm_budget_bytes=8 << 30, max_batch=32, streams=2, size_ratio=4)
+    rng = np.random.default_rng(3)
+    made = [_make(mats, rng) for _ in range(40)]
+    reqs = [srv.submit(mid, X, to_host=True) for mid, X in made]
+    for r in reqs:
+        r.wait(60)
+    srv.stop()
+    for r in reqs:
+        assert r.Y.numpy().tobytes() == _alone(mats[r.mid], r.X).numpy().tobytes()
+    assert reqs[0].t_launch <= min(r.t_launch for r in reqs[1:])
