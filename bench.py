@@ -372,6 +372,39 @@ def tune_launch(sell, h, xd, yd, stream, flags=0, blocks=(128, 256), unrolls=(1,
     return c[0], c[1], c[2], t
 
 
+def laplace_section(sell, stream, reps=2000):
+    """The 5-point Laplacian on 64 x 64 (N = 4096, 20,224 nnz), SELL-32-1: an
+    L2-resident product bound by launch latency, so the number is the time
+    per call, back to back on one stream and inside one CUDA graph."""
+    import torch
+    from paper_1307_6209_gb300 import synth
+    A = synth.laplace2d(64)
+    h = sell.sell_build(A, C=32, sigma=1, stream=stream)
+    x = torch.from_numpy(synth.vector(A.ncols, seed=0)).cuda()
+    y = torch.empty(A.nrows, dtype=torch.float64, device="cuda")
+    eager = time_spmv(sell, h, x, y, stream, reps=reps)
+    g = torch.cuda.CUDAGraph()
+    per_graph = 100
+    with torch.cuda.stream(stream):
+        sell.sell_spmv(h, x, y, stream=stream)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=stream):
+            for _ in range(per_graph):
+                sell.sell_spmv(h, x, y, stream=torch.cuda.current_stream())
+        g.replay()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps // per_graph):
+            g.replay()
+        b.record(stream)
+        b.synchronize()
+    graph = a.elapsed_time(b) * 1e-3 / (reps // per_graph * per_graph)
+    h.free()
+    return {"workload": "5-point Laplacian 64x64, N=4096, nnz=20224, SELL-32-1", "us_per_call": round(eager * 1e6, 2),
+            "us_per_call_in_graph": round(graph * 1e6, 2), "gflops": round(2.0 * A.nnz / eager / 1e9, 2)}
+
+
 def stencil_section(sell, model, stream, peak, fma_tf, n=200):
     """27-point stencil on n^3 (generated on the device): binary64, binary32 and
     bfloat16 storage, each with its tuned launch."""
@@ -767,7 +800,8 @@ def run_ours(args):
         torch.cuda.empty_cache()
         if not args.no_extras and args.workload == "lognormal" and rank == 0:
             # each extra section reports its own failure instead of losing the line
-            for key, fn in (("stencil27", lambda: stencil_section(sell, model, stream, peak, fma_tf)),
+            for key, fn in (("laplace64", lambda: laplace_section(sell, stream)),
+                            ("stencil27", lambda: stencil_section(sell, model, stream, peak, fma_tf)),
                             ("pathological", lambda: pathological_section(sell, model, stream, peak)),
                             ("batched", lambda: batched_section(sell, autotune, stream)),
                             ("serving", lambda: serving_section(sell, stream))):

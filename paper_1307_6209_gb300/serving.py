@@ -16,6 +16,7 @@ the device).
 """
 from __future__ import annotations
 
+import gc
 import threading
 import time
 from dataclasses import dataclass, field
@@ -222,9 +223,29 @@ class _Consumer:
             raise self.errors[0]
 
 
+class _NoGC:
+    """Python's cyclic garbage collector paused for a load run (a collection
+    pass over a large heap stalls the submitting thread for milliseconds and
+    turns Poisson arrivals into bursts)."""
+
+    def __enter__(self):
+        gc.collect()
+        self.was = gc.isenabled()
+        gc.disable()
+
+    def __exit__(self, *exc):
+        if self.was:
+            gc.enable()
+
+
 def burst_load(server: Server, n: int, make_request, seed: int = 0, to_host: bool = True):
     """Submit n requests at once; returns (requests, seconds until the last
     completed)."""
+    with _NoGC():
+        return _burst_load(server, n, make_request, seed, to_host)
+
+
+def _burst_load(server, n, make_request, seed, to_host):
     rng = np.random.default_rng(seed)
     c = _Consumer(server)
     t0 = time.perf_counter()
@@ -242,6 +263,11 @@ def poisson_load(server: Server, rate_hz: float, duration_s: float, make_request
     """Submit requests with exponential inter-arrival times for duration_s;
     make_request(rng) -> (mid, pinned X); a consumer thread takes the
     results as they arrive.  Returns the requests, all complete."""
+    with _NoGC():
+        return _poisson_load(server, rate_hz, duration_s, make_request, seed, to_host)
+
+
+def _poisson_load(server, rate_hz, duration_s, make_request, seed, to_host):
     rng = np.random.default_rng(seed)
     reqs = []
     c = _Consumer(server)

@@ -219,3 +219,29 @@ def test_bulk_staged_bitwise_equal(name, A):
         ref, scale, rl = oracle_reference(A, x)
         assert np.all(np.abs(np.frombuffer(outs[2][0]) - ref) <= tol_f64(rl, scale))
         h.free()
+
+
+def test_spmv_in_cuda_graph():
+    """sell_spmv captured in a CUDA graph (long rows included: their counters
+    reset themselves, so replays need no clearing) gives the eager bits on
+    every replay."""
+    import torch
+    from paper_1307_6209_gb300 import sell
+
+    A = synth.lognormal(20000, seed=12, cap=3000)
+    h = sell.sell_build(A, C=32, sigma=10 ** 9)
+    x = torch.from_numpy(synth.vector(A.ncols, seed=2)).cuda()
+    y_eager = torch.empty(A.nrows, dtype=torch.float64, device="cuda")
+    sell.sell_spmv(h, x, y_eager)  # also sizes the long-row scratch before the capture
+    torch.cuda.synchronize()
+    y = torch.full((A.nrows,), float("nan"), dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        for _ in range(3):
+            sell.sell_spmv(h, x, y, stream=s)
+    for _ in range(4):
+        y.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        assert y.cpu().numpy().tobytes() == y_eager.cpu().numpy().tobytes()
