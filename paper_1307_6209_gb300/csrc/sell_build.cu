@@ -339,7 +339,7 @@ __global__ void k_long_nseg(const int32_t *__restrict__ cl, const int32_t *__res
                             int64_t nlong, int32_t *__restrict__ nseg) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nlong; i += stride)
-        nseg[i] = (cl[lchunk[i]] + kSeg - 1) / kSeg;
+        nseg[i] = (cl[lchunk[i]] - 1) / kSeg + 1;  // cl > kSeg for a long chunk
 }
 
 __global__ void k_long_units(const int32_t *__restrict__ nseg, const int64_t *__restrict__ ubase,

@@ -279,10 +279,10 @@ __device__ __forceinline__ void long_unit(const VT *__restrict__ val, const int3
         l = t;
         s = us.y;
     } else {  // the chunk's threads take consecutive segments of each long row
-        const int i = us.y * C + t;
-        const int k = i / meta.z;
+        const int64_t i = (int64_t)us.y * C + t;  // beyond 32 bits for rows of more than 2^31 / C segments
+        const int64_t k = i / meta.z;
         if (k >= meta.x) return;
-        s = i - k * meta.z;
+        s = (int)(i - k * meta.z);
         l = lrow[(int64_t)us.x * C + k];
     }
     const int64_t c = lchunk[us.x];
@@ -290,7 +290,7 @@ __device__ __forceinline__ void long_unit(const VT *__restrict__ val, const int3
     if (r >= N) return;
     const int L = srl[r];
     if (L <= kSeg) return;  // short rows belong to the per-row path
-    const int nseg = (L + kSeg - 1) / kSeg;
+    const int nseg = (L - 1) / kSeg + 1;  // L > kSeg here; no overflow near 2^31
     if (s >= nseg) return;
     const int64_t u0 = u - us.y;  // the chunk's first unit; segment s's partial sits in unit u0 + s
     const int64_t out = perm ? (int64_t)perm[r] : r;
