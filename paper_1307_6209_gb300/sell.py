@@ -242,7 +242,35 @@ def sell_build(A, C: int = 32, sigma: int = 1, store_type: int = SELL_F64, flags
     return SellMatrix(out.value)
 
 
+def _check_vec(h: SellMatrix, t, name: str, host: bool, rows: bool = True):
+    """The element type and placement the C call expects (binary64 for F64
+    handles, binary32 otherwise; device memory unless host I/O; unit stride
+    along the right-hand sides)."""
+    if t is None or isinstance(t, int):
+        return
+    want64 = h.info.store_type == SELL_F64
+    if isinstance(t, np.ndarray):
+        ok = t.dtype == (np.float64 if want64 else np.float32)
+        if not ok:
+            raise TypeError(f"{name}: expected {'float64' if want64 else 'float32'}, got {t.dtype}")
+        if not host:
+            raise TypeError(f"{name}: a numpy array needs SELL_SPMV_HOST_IO")
+        inner = t.strides[-1] // t.itemsize if t.ndim > 1 else 1
+    else:
+        import torch
+        if t.dtype != (torch.float64 if want64 else torch.float32):
+            raise TypeError(f"{name}: expected {'float64' if want64 else 'float32'}, got {t.dtype}")
+        if t.is_cuda == host:
+            raise TypeError(f"{name}: {'host' if host else 'device'} memory expected")
+        inner = t.stride(-1) if t.dim() > 1 else t.stride(0)
+    if inner != 1:
+        raise ValueError(f"{name}: the right-hand sides must be contiguous in each row (unit inner stride)")
+
+
 def sell_spmv(h: SellMatrix, x, y, flags: int = 0, stream=None):
+    host = bool(int(flags) & SELL_SPMV_HOST_IO)
+    _check_vec(h, x, "x", host)
+    _check_vec(h, y, "y", host)
     _check(load().sell_spmv(h.handle, _ptr(x), _ptr(y), int(flags), _stream_ptr(stream)))
     return y
 
@@ -255,6 +283,9 @@ def sell_spmv_dot(h: SellMatrix, x, y, dot, flags: int = 0, stream=None):
 
 def sell_spmmv(h: SellMatrix, X, Y, flags: int = 0, stream=None, ldx=None, ldy=None, k=None):
     """Y = A X for row-major X (ncols x k) and Y (nrows x k)."""
+    host = bool(int(flags) & SELL_SPMV_HOST_IO)
+    _check_vec(h, X, "X", host)
+    _check_vec(h, Y, "Y", host)
     k = int(X.shape[1]) if k is None else int(k)
     ldx = int(X.stride(0) if hasattr(X, "stride") and callable(X.stride) else X.strides[0] // X.itemsize) \
         if ldx is None else int(ldx)

@@ -111,3 +111,27 @@ def test_failing_allocator_reports_enomem_without_leak():
             assert not live, f"leak after failing request {k}"
     finally:
         assert lib.sell_set_allocator(sell.ALLOC_FN(), sell.FREE_FN(), None) == sell.SELL_OK
+
+
+def test_binding_refuses_mismatched_buffers():
+    """The Python binding checks what the C call cannot see: element type,
+    host/device placement and a unit stride along the right-hand sides."""
+    import numpy as np
+    import torch
+    from paper_1307_6209_gb300 import sell
+
+    A = synth.laplace2d(16)
+    h = sell.sell_build(A, C=32)
+    x32 = torch.zeros(A.ncols, dtype=torch.float32, device="cuda")
+    y = torch.zeros(A.nrows, dtype=torch.float64, device="cuda")
+    with pytest.raises(TypeError):
+        sell.sell_spmv(h, x32, y)  # binary32 x for binary64 storage
+    with pytest.raises(TypeError):
+        sell.sell_spmv(h, np.zeros(A.ncols), np.zeros(A.nrows))  # host arrays without HOST_IO
+    with pytest.raises(TypeError):
+        sell.sell_spmv(h, torch.zeros(A.ncols, dtype=torch.float64, device="cuda"), np.zeros(A.nrows),
+                       flags=sell.SELL_SPMV_HOST_IO)  # device x with HOST_IO
+    X = torch.zeros((A.ncols, 8), dtype=torch.float64, device="cuda")
+    Y = torch.zeros((A.nrows, 4), dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        sell.sell_spmmv(h, X[:, ::2], Y)  # every other column: not contiguous along k
