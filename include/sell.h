@@ -333,6 +333,9 @@ typedef struct {
                              the oldest request, then later ones whose work (stored elements x k) is
                              within a factor r of it, so small requests do not wait for a large one */
     int32_t reserved;     /* 0 */
+    int64_t max_batch_work; /* 0: no cap; w > 0: with size_ratio <= 1, a batch stops taking requests
+                               once its work (stored elements x k) would exceed w (it always takes
+                               at least one) */
 } sell_server_opts;
 
 typedef struct {

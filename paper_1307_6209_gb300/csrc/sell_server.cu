@@ -124,6 +124,7 @@ struct sell_server {
     int device = 0;
     int64_t budget = 0, resident = 0, arena_bytes = 0, used = 0, peak_used = 0;
     int32_t max_batch = 64, nstreams = 3, size_ratio = 0;
+    int64_t max_work = 0;  // cap on a batch's work (stored elements x k), 0: none
     sell::Allocator al;
     char *arena_base = nullptr;
     sell::Arena arena;
@@ -285,12 +286,16 @@ void scheduler(sell_server *S) {
         if (!S->free_streams.empty() && !S->queue.empty()) {
             std::vector<Req *> batch;
             if (S->size_ratio <= 1) {
+                double bw = 0;  // the batch's work so far
                 while (!S->queue.empty() && (int)batch.size() < S->max_batch) {
                     Req *r = S->queue.front();
+                    const double w = work(S, r);
+                    if (!batch.empty() && S->max_work > 0 && bw + w > (double)S->max_work) break;
                     if (!reserve(S, r)) break;
                     S->queue.pop_front();
                     r->state = kRunning;
                     batch.push_back(r);
+                    bw += w;
                 }
             } else {
                 Req *head = S->queue.front();
@@ -373,7 +378,8 @@ extern "C" {
 
 sell_status sell_server_create(const sell_handle *mats, int32_t n, const sell_server_opts *o, sell_server_t *out) {
     if (!mats || n < 1 || !o || !out) return fail(SELL_EINVAL, "sell_server_create: bad arguments");
-    if (o->max_batch < 1 || o->max_batch > 4096 || o->streams < 1 || o->streams > 16 || o->size_ratio < 0)
+    if (o->max_batch < 1 || o->max_batch > 4096 || o->streams < 1 || o->streams > 16 || o->size_ratio < 0 ||
+        o->max_batch_work < 0)
         return fail(SELL_EINVAL,
                     "sell_server_create: need 1 <= max_batch <= 4096, 1 <= streams <= 16, size_ratio >= 0");
     sell_server *S = new (std::nothrow) sell_server();
@@ -402,6 +408,7 @@ sell_status sell_server_create(const sell_handle *mats, int32_t n, const sell_se
     S->max_batch = o->max_batch;
     S->nstreams = o->streams;
     S->size_ratio = o->size_ratio;
+    S->max_work = o->max_batch_work;
     S->al = current_allocator();
     S->arena_base = static_cast<char *>(S->al.get((size_t)S->arena_bytes, nullptr));
     if (!S->arena_base) {

@@ -89,13 +89,14 @@ class Request:
 class Server:
     """Native server over resident matrices `mats` (list of SellMatrix)."""
 
-    def __init__(self, mats, hbm_budget_bytes: int, max_batch: int = 128, streams: int = 6, size_ratio: int = 0):
+    def __init__(self, mats, hbm_budget_bytes: int, max_batch: int = 128, streams: int = 6, size_ratio: int = 0,
+                 max_batch_work: int = 0):
         self.mats = list(mats)
         self.resident = sum(h.info.device_bytes for h in self.mats)
         if self.resident >= hbm_budget_bytes:
             raise ValueError("resident matrices fill the HBM budget")
         self.budget = int(hbm_budget_bytes)
-        self.handle = sell.sell_server_create(self.mats, self.budget, max_batch, streams, size_ratio)
+        self.handle = sell.sell_server_create(self.mats, self.budget, max_batch, streams, size_ratio, max_batch_work)
         self._done = []
         self._done_lock = threading.Lock()
         self._pending = {}  # id -> Request, until collected
