@@ -10,9 +10,11 @@
 //   L >  kSeg : the row is cut into segments of kSeg consecutive entries;
 //               segment 0 is a chain starting at y0, every other segment a
 //               chain starting at 0; the segment results are then added in
-//               segment order (Dot2: merged with TwoSum, errors carried) --
-//               for more than kSuper (256) segments, first within each group
-//               of kSuper consecutive segments, then the group results in order.
+//               segment order (binary32 chains: in binary64, rounded to
+//               binary32 once at the end; Dot2: merged with TwoSum, errors
+//               carried) -- for more than kSuper (256) segments, first within
+//               each group of kSuper consecutive segments, then the group
+//               results in order.
 // Every segment of a long row is an independent work unit, so long rows are
 // spread over the whole grid instead of holding one warp for their full
 // length (Sec. 3.4 notes that one thread per row leaves a warp waiting for
@@ -82,6 +84,26 @@ struct Dot2 {
         r.p = t.x;
         r.e = t.y;
         return r;
+    }
+};
+
+// The type a long row's segment partials are kept and folded in.  Binary32
+// chains (Plain<float>) are folded in binary64 -- a segment result converts
+// exactly, the fold rounds in binary64, and the row's result is rounded to
+// binary32 once at the end; binary64 and Dot2 fold in their own type.  Every
+// partial slot of the scratch is 8 bytes, so both fit.
+template <class Acc>
+struct PartOf {
+    using T = Acc;
+    __device__ __forceinline__ static T from(const Acc &a) { return a; }
+};
+template <>
+struct PartOf<Plain<float>> {
+    using T = Plain<double>;
+    __device__ __forceinline__ static T from(const Plain<float> &a) {
+        T t;
+        t.s = (double)a.s;
+        return t;
     }
 };
 
@@ -300,15 +322,17 @@ __device__ __forceinline__ void long_unit(const VT *__restrict__ val, const int3
     const int64_t base = cs[c] + l;
     chain<VT, XT, K, U, PIPE, Acc>(acc, val + base, col + base, C, s * kSeg, min(L, (s + 1) * kSeg), X, ldx,
                                    vec, pol);
+    using PT = typename PartOf<Acc>::T;
+    PT *pp = reinterpret_cast<PT *>(part);
 #pragma unroll
-    for (int q = 0; q < K; ++q) part[((u0 + s) * C + l) * K + q] = acc[q];
+    for (int q = 0; q < K; ++q) pp[((u0 + s) * C + l) * K + q] = PartOf<Acc>::from(acc[q]);
     int32_t *ct = cnt + (int64_t)us.x * C + l;
-    Acc tot[K];
+    PT tot[K];
     if (nseg <= kSuper) {
         __threadfence();
         if (atomicAdd(ct, 1) != nseg - 1) return;
         __threadfence();  // this thread completed the row
-        fold_partials<K, Acc>(part, u0, 1, nseg, C, l, tot);
+        fold_partials<K, PT>(pp, u0, 1, nseg, C, l, tot);
     } else {
         const int s0 = (s / kSuper) * kSuper;
         const int ng = min(kSuper, nseg - s0);
@@ -316,18 +340,18 @@ __device__ __forceinline__ void long_unit(const VT *__restrict__ val, const int3
         __threadfence();
         if (atomicAdd(cg, 1) != ng - 1) return;
         __threadfence();  // this thread completed the group
-        fold_partials<K, Acc>(part, u0 + s0, 1, ng, C, l, tot);
+        fold_partials<K, PT>(pp, u0 + s0, 1, ng, C, l, tot);
         *cg = 0;
 #pragma unroll
-        for (int q = 0; q < K; ++q) part[((u0 + s0) * C + l) * K + q] = tot[q];
+        for (int q = 0; q < K; ++q) pp[((u0 + s0) * C + l) * K + q] = tot[q];
         __threadfence();
         const int ngroups = (nseg + kSuper - 1) / kSuper;
         if (atomicAdd(ct, 1) != ngroups - 1) return;
         __threadfence();  // ... and the last group of the row
-        fold_partials<K, Acc>(part, u0, kSuper, ngroups, C, l, tot);
+        fold_partials<K, PT>(pp, u0, kSuper, ngroups, C, l, tot);
     }
 #pragma unroll
-    for (int q = 0; q < K; ++q) Y[out * ldy + q] = tot[q].result();
+    for (int q = 0; q < K; ++q) Y[out * ldy + q] = static_cast<XT>(tot[q].result());
     *ct = 0;
 }
 

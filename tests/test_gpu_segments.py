@@ -96,3 +96,76 @@ def test_f64_rows_match_documented_arithmetic(accumulate, spread):
         got = yd.cpu().numpy()
         bad = np.nonzero(got.view(np.uint64) != expect.view(np.uint64))[0]
         assert bad.size == 0, f"C={C} sigma={sigma} pipeline={pipe}: rows {bad[:8]} (lengths {np.diff(A.rpt)[bad[:8]]})"
+
+
+def _round_f32(q: Fraction) -> float:
+    """q rounded to the nearest binary32 (ties to even), exactly."""
+    if q == 0:
+        return 0.0
+    sign = -1.0 if q < 0 else 1.0
+    q = abs(q)
+    e = q.numerator.bit_length() - q.denominator.bit_length()  # 2^(e-1) <= q < 2^(e+1)
+    if Fraction(2) ** e > q:
+        e -= 1
+    e = max(e, -126)  # subnormals share the exponent of the smallest normal
+    scale = Fraction(2) ** (e - 23)  # spacing of binary32 numbers in [2^e, 2^(e+1))
+    m = q / scale
+    n = m.numerator // m.denominator
+    rem = m - n
+    if rem > Fraction(1, 2) or (rem == Fraction(1, 2) and n % 2 == 1):
+        n += 1
+    return sign * float(n * scale)
+
+
+def _row_result_f32(vals, xs, y0):
+    """Binary32 FMA chains per 64-entry segment, the segment results added in
+    order in binary64 (two levels beyond 256 segments), one final rounding to
+    binary32."""
+    def chain(v, x, s):
+        s = float(s)
+        for a, b in zip(v, x):
+            s = _round_f32(Fraction(float(a)) * Fraction(float(b)) + Fraction(s))
+        return s
+    L = len(vals)
+    if L <= SEG:
+        return chain(vals, xs, y0)
+    parts = [chain(vals[s:s + SEG], xs[s:s + SEG], y0 if s == 0 else 0.0) for s in range(0, L, SEG)]
+
+    def fold(ps):
+        t = ps[0]
+        for p in ps[1:]:
+            t = _rnd(Fraction(t) + Fraction(p))
+        return t
+    t = fold(parts) if len(parts) <= SUPER else fold([fold(parts[g:g + SUPER]) for g in range(0, len(parts), SUPER)])
+    return float(np.float32(t))
+
+
+def test_f32_long_rows_fold_in_binary64():
+    """Binary32 storage: long rows' segment results are added in binary64 and
+    rounded once; checked bit for bit against exact rational emulation."""
+    import torch
+    import oracle
+    from paper_1307_6209_gb300 import sell
+
+    rng = np.random.default_rng(5)
+    n = 40000
+    lens = [3, 64, 65, 300, 1000, 5000, 17000] + [int(v) for v in rng.integers(0, 30, 57)]
+    rows = [np.sort(rng.choice(n, size=L, replace=False)) for L in lens]
+    rl = np.array([len(r) for r in rows])
+    col = np.concatenate(rows).astype(np.int32)
+    val = rng.standard_normal(col.shape[0])
+    rpt = np.zeros(len(rows) + 1, np.int64)
+    np.cumsum(rl, out=rpt[1:])
+    A = synth.CSR(len(rows), n, rpt, col, val)
+    v32 = oracle.round_values(A.val, oracle.F32).astype(np.float32)
+    x = synth.vector(n, seed=3).astype(np.float32)
+    expect = np.array([_row_result_f32(v32[rpt[i]:rpt[i + 1]], x[col[rpt[i]:rpt[i + 1]]], 0.0)
+                       for i in range(len(rows))], dtype=np.float32)
+    for C, sigma in [(32, 1), (32, 10 ** 9), (64, 4)]:
+        h = sell.sell_build(A, C=C, sigma=sigma, store_type=sell.SELL_F32)
+        y = torch.empty(len(rows), dtype=torch.float32, device="cuda")
+        sell.sell_spmv(h, torch.from_numpy(x).cuda(), y)
+        torch.cuda.synchronize()
+        got = y.cpu().numpy()
+        bad = np.nonzero(got.view(np.uint32) != expect.view(np.uint32))[0]
+        assert bad.size == 0, f"C={C} sigma={sigma}: rows {bad[:8]} (lengths {rl[bad[:8]]})"
