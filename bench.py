@@ -783,7 +783,8 @@ def run_ours(args):
                 hm = sell.sell_build(csr_d, C=C, sigma=sigma, store_type=st, stream=stream)
                 y32 = torch.empty(A.nrows, dtype=torch.float32, device="cuda")
                 row = {}
-                for tag, fl in (("plain", 0), ("dot2", sell.SELL_SPMV_COMPENSATED)):
+                for tag, fl in (("plain", 0), ("dot2", sell.SELL_SPMV_COMPENSATED),
+                                ("dot2_long_rows", sell.SELL_SPMV_COMPENSATED_LONG)):
                     blk, unr, pip, _ = tune_launch(sell, hm, x32, y32, stream, flags=fl)
                     dt = time_spmv(sell, hm, x32, y32, stream, reps=100, flags=fl)
                     torch.cuda.synchronize()

@@ -150,6 +150,11 @@ SELL_API sell_status sell_build(const sell_csr *A, const sell_opts *opts, void *
 
 /* SpMV flags. */
 #define SELL_SPMV_ACCUMULATE 0x1u   /* y = y + A x instead of y = A x */
+#define SELL_SPMV_COMPENSATED_LONG 0x8u /* F32/BF16 storage: compensated (Dot2)
+                                          accumulation only for rows of more
+                                          than 64 entries (the long-row path);
+                                          shorter rows keep the binary32 chain.
+                                          SELL_SPMV_COMPENSATED takes precedence */
 #define SELL_SPMV_COMPENSATED 0x2u  /* F32/BF16 storage: compensated (Dot2)
                                        binary32 accumulation of each row */
 #define SELL_SPMV_HOST_IO 0x4u      /* x and y (X and Y) are host pointers
@@ -170,12 +175,15 @@ SELL_API sell_status sell_build(const sell_csr *A, const sell_opts *opts, void *
  * fused multiply-adds.
  * Types: F64 storage -> x, y binary64; F32/BF16 storage -> x, y binary32 with
  * binary32 accumulation (SELL_SPMV_COMPENSATED: error-free product and sum
- * transformations, result rounded once).
+ * transformations, result rounded once; SELL_SPMV_COMPENSATED_LONG: the same
+ * for rows of more than 64 entries only).  The segment sums of long rows are
+ * added in binary64 for binary32 chains.
  * x has ncols elements and y nrows, both in the original row order unless the
  * handle was built with SELL_BUILD_PERMUTE_COLS (then both in sorted order).
  * x and y must not overlap.  Asynchronous on `stream`.
  * Errors: SELL_EINVAL (NULL handle/pointer), SELL_EUNSUPPORTED (COMPENSATED
- * on F64 storage), SELL_ENOMEM (HOST_IO staging), SELL_ECUDA. */
+ * or COMPENSATED_LONG on F64 storage), SELL_ENOMEM (HOST_IO staging),
+ * SELL_ECUDA. */
 SELL_API sell_status sell_spmv(sell_handle h, const void *x, void *y, uint32_t flags, void *stream);
 
 /* y = A x (as sell_spmv, same flags but SELL_SPMV_HOST_IO) followed by
@@ -279,7 +287,7 @@ typedef struct {
     void *Y;
     int64_t ldx, ldy;
     int32_t k;
-    uint32_t flags;  /* SELL_SPMV_ACCUMULATE | SELL_SPMV_COMPENSATED */
+    uint32_t flags;  /* SELL_SPMV_ACCUMULATE | SELL_SPMV_COMPENSATED | SELL_SPMV_COMPENSATED_LONG */
 } sell_batch_item;
 
 typedef struct sell_batch *sell_batch_plan;

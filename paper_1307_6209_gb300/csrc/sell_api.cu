@@ -189,9 +189,9 @@ sell_status sell_spmmv(sell_handle h, const void *X, int64_t ldx, void *Y, int64
                        uint32_t flags, void *stream) {
     if (!h) return fail(SELL_EINVAL, "sell_spmmv: NULL handle");
     if (k < 1 || ldx < k || ldy < k) return fail(SELL_EINVAL, "sell_spmmv: need k >= 1, ldx >= k, ldy >= k");
-    if (flags & ~(SELL_SPMV_ACCUMULATE | SELL_SPMV_COMPENSATED | SELL_SPMV_HOST_IO))
+    if (flags & ~(SELL_SPMV_ACCUMULATE | kCompFlags | SELL_SPMV_HOST_IO))
         return fail(SELL_EINVAL, "sell_spmmv: unknown flags");
-    if ((flags & SELL_SPMV_COMPENSATED) && h->store_type == SELL_F64)
+    if ((flags & kCompFlags) && h->store_type == SELL_F64)
         return fail(SELL_EUNSUPPORTED, "compensated accumulation needs F32/BF16 storage");
     if (h->nrows == 0) return SELL_OK;
     if (!Y || (!X && h->ncols > 0)) return fail(SELL_EINVAL, "sell_spmmv: NULL vector");

@@ -65,7 +65,7 @@ struct LaunchParams {
 
 // One block per work unit, long-row units first in the grid so that they
 // start early (the same shape as the single-product kernel).
-template <class VT, int K, class Acc>
+template <class VT, int K, class Acc, class AccL = Acc>
 __global__ void __launch_bounds__(kTileRows)
 k_batch(const __grid_constant__ LaunchParams lp) {
     using XT = typename XType<VT>::T;
@@ -85,8 +85,8 @@ k_batch(const __grid_constant__ LaunchParams lp) {
     if (is_long) {
         const int64_t v = first + threadIdx.x;
         if (v < P.long_threads)
-            long_unit<VT, XT, K, U, false, Acc>(static_cast<const VT *>(P.val), P.col, P.cs, P.srl, P.perm, P.lchunk,
-                                         P.lunit, P.lmeta, P.lrow, static_cast<Acc *>(P.part), P.cnt, P.cnt2,
+            long_unit<VT, XT, K, U, false, AccL>(static_cast<const VT *>(P.val), P.col, P.cs, P.srl, P.perm,
+                                         P.lchunk, P.lunit, P.lmeta, P.lrow, static_cast<AccL *>(P.part), P.cnt, P.cnt2,
                                          static_cast<const XT *>(P.X),
                                          P.ldx, static_cast<XT *>(P.Y), P.ldy, P.N, P.C, v, P.acc, P.vec != 0, pol);
         return;
@@ -100,20 +100,28 @@ k_batch(const __grid_constant__ LaunchParams lp) {
 
 using KernelFn = void (*)(const LaunchParams);
 
-template <class VT, class Acc>
+template <class VT, class Acc, class AccL = Acc>
 KernelFn kernel_for_k(int kb) {
     switch (kb) {
-        case 1: return k_batch<VT, 1, Acc>;
-        case 2: return k_batch<VT, 2, Acc>;
-        case 4: return k_batch<VT, 4, Acc>;
-        default: return k_batch<VT, 8, Acc>;
+        case 1: return k_batch<VT, 1, Acc, AccL>;
+        case 2: return k_batch<VT, 2, Acc, AccL>;
+        case 4: return k_batch<VT, 4, Acc, AccL>;
+        default: return k_batch<VT, 8, Acc, AccL>;
     }
+}
+
+// comp: 0 binary32 chains, 1 Dot2 on every row, 2 Dot2 on the long rows only.
+template <class VT>
+KernelFn kernel_for_reduced(int comp, int kb) {
+    if (comp == 1) return kernel_for_k<VT, Dot2>(kb);
+    if (comp == 2) return kernel_for_k<VT, Plain<float>, Dot2>(kb);
+    return kernel_for_k<VT, Plain<float>>(kb);
 }
 
 KernelFn kernel_for(int type, int comp, int kb) {
     if (type == SELL_F64) return kernel_for_k<double, Plain<double>>(kb);
-    if (type == SELL_F32) return comp ? kernel_for_k<float, Dot2>(kb) : kernel_for_k<float, Plain<float>>(kb);
-    return comp ? kernel_for_k<__nv_bfloat16, Dot2>(kb) : kernel_for_k<__nv_bfloat16, Plain<float>>(kb);
+    if (type == SELL_F32) return kernel_for_reduced<float>(comp, kb);
+    return kernel_for_reduced<__nv_bfloat16>(comp, kb);
 }
 
 }  // namespace
@@ -167,9 +175,9 @@ sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s
         if (it.k < 1 || it.ldx < it.k || it.ldy < it.k)
             return fail(SELL_EINVAL, "sell_batch_create: need k >= 1, ldx >= k, ldy >= k");
         if (h->nrows > 0 && (!it.X || !it.Y)) return fail(SELL_EINVAL, "sell_batch_create: NULL X/Y");
-        if (it.flags & ~(SELL_SPMV_ACCUMULATE | SELL_SPMV_COMPENSATED))
+        if (it.flags & ~(SELL_SPMV_ACCUMULATE | kCompFlags))
             return fail(SELL_EINVAL, "sell_batch_create: unsupported flags");
-        if ((it.flags & SELL_SPMV_COMPENSATED) && h->store_type == SELL_F64)
+        if ((it.flags & kCompFlags) && h->store_type == SELL_F64)
             return fail(SELL_EUNSUPPORTED, "compensated accumulation needs F32/BF16 storage");
         if (h->nrows == 0) continue;
         size_t coff = 0;
@@ -215,7 +223,7 @@ sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s
             P.kb = kb;
             P.type = h->store_type;
             P.acc = (it.flags & SELL_SPMV_ACCUMULATE) ? 1 : 0;
-            P.comp = (it.flags & SELL_SPMV_COMPENSATED) && h->store_type != SELL_F64 ? 1 : 0;
+            P.comp = h->store_type != SELL_F64 ? comp_mode(it.flags) : 0;
             P.vec = (((uintptr_t)P.X % 16) == 0 && ((it.ldx * xs) % 16) == 0) ? 1 : 0;
             prods.push_back(P);
             owner.push_back(h);

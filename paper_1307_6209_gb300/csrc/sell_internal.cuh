@@ -58,6 +58,14 @@ struct DevBuf {
 
 inline size_t value_size(int t) { return t == SELL_F64 ? 8 : (t == SELL_F32 ? 4 : 2); }
 
+// Accumulation of reduced-precision products: 0 binary32 chains, 1 Dot2 on
+// every row, 2 Dot2 on rows longer than kSeg only.
+inline int comp_mode(uint32_t flags) {
+    if (flags & SELL_SPMV_COMPENSATED) return 1;
+    return (flags & SELL_SPMV_COMPENSATED_LONG) ? 2 : 0;
+}
+constexpr uint32_t kCompFlags = SELL_SPMV_COMPENSATED | SELL_SPMV_COMPENSATED_LONG;
+
 }  // namespace sell
 
 // ------------------------------------------------------------------ handle

@@ -54,10 +54,10 @@ extern "C" sell_status sell_spmmv_noalloc(sell_handle h, const void *X, int64_t 
     if (!h) return fail(SELL_EINVAL, "sell_spmmv_noalloc: NULL handle");
     if (k < 1 || ldx < k || ldy < k)
         return fail(SELL_EINVAL, "sell_spmmv_noalloc: need k >= 1, ldx >= k, ldy >= k");
-    if (flags & ~(SELL_SPMV_ACCUMULATE | SELL_SPMV_COMPENSATED))
+    if (flags & ~(SELL_SPMV_ACCUMULATE | kCompFlags))
         return fail(SELL_EINVAL, "sell_spmmv_noalloc: only ACCUMULATE and COMPENSATED are accepted "
                                  "(HOST_IO needs staging memory)");
-    if ((flags & SELL_SPMV_COMPENSATED) && h->store_type == SELL_F64)
+    if ((flags & kCompFlags) && h->store_type == SELL_F64)
         return fail(SELL_EUNSUPPORTED, "compensated accumulation needs F32/BF16 storage");
     if (h->nrows == 0) return SELL_OK;
     if (!Y || (!X && h->ncols > 0)) return fail(SELL_EINVAL, "sell_spmmv_noalloc: NULL vector");

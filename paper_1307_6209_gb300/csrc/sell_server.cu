@@ -456,10 +456,10 @@ sell_status sell_server_submit(sell_server_t S, int32_t mid, const void *X, int3
     if (!S || !id) return fail(SELL_EINVAL, "sell_server_submit: NULL argument");
     if (mid < 0 || mid >= (int32_t)S->mats.size()) return fail(SELL_EINVAL, "sell_server_submit: bad matrix id");
     if (k < 1) return fail(SELL_EINVAL, "sell_server_submit: need k >= 1");
-    if (flags & ~(SELL_SPMV_ACCUMULATE | SELL_SPMV_COMPENSATED))
+    if (flags & ~(SELL_SPMV_ACCUMULATE | kCompFlags))
         return fail(SELL_EINVAL, "sell_server_submit: unsupported flags");
     const sell_matrix *h = S->mats[mid];
-    if ((flags & SELL_SPMV_COMPENSATED) && h->store_type == SELL_F64)
+    if ((flags & kCompFlags) && h->store_type == SELL_F64)
         return fail(SELL_EUNSUPPORTED, "compensated accumulation needs F32/BF16 storage");
     if ((flags & SELL_SPMV_ACCUMULATE) && !Y)
         return fail(SELL_EINVAL, "sell_server_submit: accumulating needs a host y");

@@ -11,9 +11,9 @@ namespace sell {
 cudaError_t spmv_block_f64(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy, int kb,
                            int acc, int vec, void *part, int32_t *cnt, int32_t *cnt2, cudaStream_t s);
 cudaError_t spmv_block_f32(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy, int kb,
-                           int acc, int vec, bool comp, void *part, int32_t *cnt, int32_t *cnt2, cudaStream_t s);
+                           int acc, int vec, int comp, void *part, int32_t *cnt, int32_t *cnt2, cudaStream_t s);
 cudaError_t spmv_block_bf16(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy, int kb,
-                            int acc, int vec, bool comp, void *part, int32_t *cnt, int32_t *cnt2, cudaStream_t s);
+                            int acc, int vec, int comp, void *part, int32_t *cnt, int32_t *cnt2, cudaStream_t s);
 
 int bulk_blocks_per_sm_f64(const sell_matrix *h, int W, int R);
 int bulk_blocks_per_sm_f32(const sell_matrix *h, int W, int R);
@@ -22,7 +22,7 @@ int bulk_blocks_per_sm_bf16(const sell_matrix *h, int W, int R);
 namespace {
 
 cudaError_t dispatch(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy, int kb, int acc,
-                     int vec, bool comp, void *part, int32_t *cnt, int32_t *cnt2, cudaStream_t s) {
+                     int vec, int comp, void *part, int32_t *cnt, int32_t *cnt2, cudaStream_t s) {
     switch (h->store_type) {
         case SELL_F64: return spmv_block_f64(h, X, ldx, Y, ldy, kb, acc, vec, part, cnt, cnt2, s);
         case SELL_F32: return spmv_block_f32(h, X, ldx, Y, ldy, kb, acc, vec, comp, part, cnt, cnt2, s);
@@ -49,7 +49,7 @@ sell_status launch_spmmv(sell_matrix *h, const void *X, int64_t ldx, void *Y, in
         }
     }
     const int acc = (flags & SELL_SPMV_ACCUMULATE) ? 1 : 0;
-    const bool comp = (flags & SELL_SPMV_COMPENSATED) != 0;
+    const int comp = comp_mode(flags);
     const size_t xs = h->store_type == SELL_F64 ? 8 : 4;
     int32_t done = 0;
     while (done < k) {
@@ -72,7 +72,7 @@ sell_status launch_block_with_scratch(const sell_matrix *h, const void *X, int64
                                       int64_t ldy, int kb, uint32_t flags, void *part, int32_t *cnt,
                                       int32_t *cnt2, cudaStream_t s) {
     const int acc = (flags & SELL_SPMV_ACCUMULATE) ? 1 : 0;
-    const bool comp = (flags & SELL_SPMV_COMPENSATED) != 0;
+    const int comp = comp_mode(flags);
     const size_t xs = h->store_type == SELL_F64 ? 8 : 4;
     const int vec = (((uintptr_t)X % 16) == 0 && ((ldx * xs) % 16) == 0) ? 1 : 0;
     cudaError_t e = dispatch(h, X, ldx, Y, ldy, kb, acc, vec, comp, part, cnt, cnt2, s);

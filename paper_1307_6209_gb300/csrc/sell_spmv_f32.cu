@@ -6,9 +6,11 @@
 namespace sell {
 
 cudaError_t spmv_block_f32(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy, int kb,
-                           int acc, int vec, bool comp, void *part, int32_t *cnt, int32_t *cnt2, cudaStream_t s) {
-    return comp ? spmv_block<float, Dot2>(h, X, ldx, Y, ldy, kb, acc, vec, part, cnt, cnt2, s)
-                : spmv_block<float, Plain<float>>(h, X, ldx, Y, ldy, kb, acc, vec, part, cnt, cnt2, s);
+                           int acc, int vec, int comp, void *part, int32_t *cnt, int32_t *cnt2, cudaStream_t s) {
+    if (comp == 1) return spmv_block<float, Dot2>(h, X, ldx, Y, ldy, kb, acc, vec, part, cnt, cnt2, s);
+    if (comp == 2)  // Dot2 on the long rows only
+        return spmv_block<float, Plain<float>, Dot2>(h, X, ldx, Y, ldy, kb, acc, vec, part, cnt, cnt2, s);
+    return spmv_block<float, Plain<float>>(h, X, ldx, Y, ldy, kb, acc, vec, part, cnt, cnt2, s);
 }
 
 // Resident blocks per SM of the bulk-staged kernels of this storage type.

@@ -20,6 +20,8 @@
 // gathers in flight.
 #pragma once
 
+#include <type_traits>
+
 #include "sell_rowdot.cuh"
 #include "sell_spmv_bulk.cuh"
 
@@ -27,12 +29,14 @@ namespace sell {
 namespace spmv_impl {
 
 
-template <class VT, int K, int U, bool PIPE, class Acc, bool LONG>
+// AccL: the accumulation of the long rows' segments (Acc unless only long
+// rows are compensated, SELL_SPMV_COMPENSATED_LONG).
+template <class VT, int K, int U, bool PIPE, class Acc, bool LONG, class AccL = Acc>
 __global__ void __launch_bounds__(512)
 k_spmmv(const VT *__restrict__ val, const int32_t *__restrict__ col, const int64_t *__restrict__ cs,
         const int32_t *__restrict__ srl, const int32_t *__restrict__ perm, const int32_t *__restrict__ lchunk,
         const int2 *__restrict__ lunit, const int4 *__restrict__ lmeta, const int32_t *__restrict__ lrow,
-        int64_t long_threads, int64_t long_blocks, Acc *part, int32_t *cnt,
+        int64_t long_threads, int64_t long_blocks, AccL *part, int32_t *cnt,
         int32_t *cnt2,
         const typename XType<VT>::T *__restrict__ X, int64_t ldx, typename XType<VT>::T *Y, int64_t ldy,
         int64_t N, int C, int accumulate, int vec) {
@@ -42,8 +46,8 @@ k_spmmv(const VT *__restrict__ val, const int32_t *__restrict__ col, const int64
         if (blockIdx.x < long_blocks) {
             const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
             if (v < long_threads)
-                long_unit<VT, XT, K, U, PIPE, Acc>(val, col, cs, srl, perm, lchunk, lunit, lmeta, lrow, part, cnt,
-                                                   cnt2, X, ldx, Y, ldy, N, C, v, accumulate, vec != 0, pol);
+                long_unit<VT, XT, K, U, PIPE, AccL>(val, col, cs, srl, perm, lchunk, lunit, lmeta, lrow, part, cnt,
+                                                    cnt2, X, ldx, Y, ldy, N, C, v, accumulate, vec != 0, pol);
             return;
         }
     }
@@ -54,7 +58,7 @@ k_spmmv(const VT *__restrict__ val, const int32_t *__restrict__ col, const int64
 
 // One launch of k_spmmv with the given long-row scratch (the handle's own,
 // or the caller's for sell_spmmv_noalloc).
-template <class VT, int K, int U, bool PIPE, class Acc>
+template <class VT, int K, int U, bool PIPE, class Acc, class AccL = Acc>
 cudaError_t run_with(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy, int acc,
                      int vec, void *part, int32_t *cnt, int32_t *cnt2, cudaStream_t s) {
     using XT = typename XType<VT>::T;
@@ -63,71 +67,71 @@ cudaError_t run_with(const sell_matrix *h, const void *X, int64_t ldx, void *Y, 
     const int64_t grid = long_blocks + (h->nrows + h->block - 1) / h->block;
     // without long rows the long-row path is compiled out, so that it does
     // not cost the per-row path registers or scheduling freedom
-    auto kern = h->nunits ? k_spmmv<VT, K, U, PIPE, Acc, true> : k_spmmv<VT, K, U, PIPE, Acc, false>;
+    auto kern = h->nunits ? k_spmmv<VT, K, U, PIPE, Acc, true, AccL> : k_spmmv<VT, K, U, PIPE, Acc, false, AccL>;
     kern<<<(unsigned)grid, h->block, 0, s>>>(
         static_cast<const VT *>(h->val), h->col, h->cs, h->srl,
         (h->flags & SELL_BUILD_PERMUTE_COLS) ? nullptr : h->perm, h->lchunk, h->lunit, h->lmeta, h->lrow,
-        long_threads, long_blocks, static_cast<Acc *>(part), cnt, cnt2, static_cast<const XT *>(X), ldx,
+        long_threads, long_blocks, static_cast<AccL *>(part), cnt, cnt2, static_cast<const XT *>(X), ldx,
         static_cast<XT *>(Y), ldy, h->nrows, h->C, acc, vec);
     return cudaGetLastError();
 }
 
-template <class VT, int K, int U, bool PIPE, class Acc>
+template <class VT, int K, int U, bool PIPE, class Acc, class AccL>
 cudaError_t run(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy, int acc,
                 int vec, cudaStream_t s) {
-    return run_with<VT, K, U, PIPE, Acc>(h, X, ldx, Y, ldy, acc, vec, h->part, h->cnt, h->cnt2, s);
+    return run_with<VT, K, U, PIPE, Acc, AccL>(h, X, ldx, Y, ldy, acc, vec, h->part, h->cnt, h->cnt2, s);
 }
 
-template <class VT, class Acc>
+template <class VT, class Acc, class AccL>
 cudaError_t pick_with(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy, int kb,
                       int acc, int vec, void *part, int32_t *cnt, int32_t *cnt2, cudaStream_t s) {
     switch (kb) {
-        case 1: return run_with<VT, 1, 4, false, Acc>(h, X, ldx, Y, ldy, acc, vec, part, cnt, cnt2, s);
-        case 2: return run_with<VT, 2, 4, false, Acc>(h, X, ldx, Y, ldy, acc, vec, part, cnt, cnt2, s);
-        case 4: return run_with<VT, 4, 2, false, Acc>(h, X, ldx, Y, ldy, acc, vec, part, cnt, cnt2, s);
-        default: return run_with<VT, 8, 2, false, Acc>(h, X, ldx, Y, ldy, acc, vec, part, cnt, cnt2, s);
+        case 1: return run_with<VT, 1, 4, false, Acc, AccL>(h, X, ldx, Y, ldy, acc, vec, part, cnt, cnt2, s);
+        case 2: return run_with<VT, 2, 4, false, Acc, AccL>(h, X, ldx, Y, ldy, acc, vec, part, cnt, cnt2, s);
+        case 4: return run_with<VT, 4, 2, false, Acc, AccL>(h, X, ldx, Y, ldy, acc, vec, part, cnt, cnt2, s);
+        default: return run_with<VT, 8, 2, false, Acc, AccL>(h, X, ldx, Y, ldy, acc, vec, part, cnt, cnt2, s);
     }
 }
 
 // Unroll choices keep U * K <= 16 gathered values per thread.
-template <class VT, int K, bool PIPE, class Acc>
+template <class VT, int K, bool PIPE, class Acc, class AccL>
 cudaError_t pick_u(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy, int acc, int vec,
                    cudaStream_t s) {
     int u = h->unroll;
     if constexpr (K >= 8) {
-        return u >= 2 ? run<VT, K, 2, PIPE, Acc>(h, X, ldx, Y, ldy, acc, vec, s)
-                      : run<VT, K, 1, PIPE, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
+        return u >= 2 ? run<VT, K, 2, PIPE, Acc, AccL>(h, X, ldx, Y, ldy, acc, vec, s)
+                      : run<VT, K, 1, PIPE, Acc, AccL>(h, X, ldx, Y, ldy, acc, vec, s);
     } else if constexpr (K >= 4) {
-        if (u >= 4) return run<VT, K, 4, PIPE, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
-        if (u >= 2) return run<VT, K, 2, PIPE, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
-        return run<VT, K, 1, PIPE, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
+        if (u >= 4) return run<VT, K, 4, PIPE, Acc, AccL>(h, X, ldx, Y, ldy, acc, vec, s);
+        if (u >= 2) return run<VT, K, 2, PIPE, Acc, AccL>(h, X, ldx, Y, ldy, acc, vec, s);
+        return run<VT, K, 1, PIPE, Acc, AccL>(h, X, ldx, Y, ldy, acc, vec, s);
     } else {
-        if (u >= 8) return run<VT, K, 8, PIPE, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
-        if (u >= 4) return run<VT, K, 4, PIPE, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
-        if (u >= 2) return run<VT, K, 2, PIPE, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
-        return run<VT, K, 1, PIPE, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
+        if (u >= 8) return run<VT, K, 8, PIPE, Acc, AccL>(h, X, ldx, Y, ldy, acc, vec, s);
+        if (u >= 4) return run<VT, K, 4, PIPE, Acc, AccL>(h, X, ldx, Y, ldy, acc, vec, s);
+        if (u >= 2) return run<VT, K, 2, PIPE, Acc, AccL>(h, X, ldx, Y, ldy, acc, vec, s);
+        return run<VT, K, 1, PIPE, Acc, AccL>(h, X, ldx, Y, ldy, acc, vec, s);
     }
 }
 
 // The software-pipelined chain is built for 1 and 2 right-hand sides (wider
 // blocks already keep many loads in flight and would double their registers).
-template <class VT, int K, class Acc>
+template <class VT, int K, class Acc, class AccL>
 cudaError_t pick_unroll(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy,
                         int acc, int vec, cudaStream_t s) {
     if constexpr (K <= 2) {
-        if (h->pipeline == 1) return pick_u<VT, K, true, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
+        if (h->pipeline == 1) return pick_u<VT, K, true, Acc, AccL>(h, X, ldx, Y, ldy, acc, vec, s);
     }
-    return pick_u<VT, K, false, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
+    return pick_u<VT, K, false, Acc, AccL>(h, X, ldx, Y, ldy, acc, vec, s);
 }
 
-template <class VT, class Acc>
+template <class VT, class Acc, class AccL>
 cudaError_t pick_k(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy, int kb,
                    int acc, int vec, cudaStream_t s) {
     switch (kb) {
-        case 1: return pick_unroll<VT, 1, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
-        case 2: return pick_unroll<VT, 2, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
-        case 4: return pick_unroll<VT, 4, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
-        default: return pick_unroll<VT, 8, Acc>(h, X, ldx, Y, ldy, acc, vec, s);
+        case 1: return pick_unroll<VT, 1, Acc, AccL>(h, X, ldx, Y, ldy, acc, vec, s);
+        case 2: return pick_unroll<VT, 2, Acc, AccL>(h, X, ldx, Y, ldy, acc, vec, s);
+        case 4: return pick_unroll<VT, 4, Acc, AccL>(h, X, ldx, Y, ldy, acc, vec, s);
+        default: return pick_unroll<VT, 8, Acc, AccL>(h, X, ldx, Y, ldy, acc, vec, s);
     }
 }
 
@@ -136,13 +140,16 @@ cudaError_t pick_k(const sell_matrix *h, const void *X, int64_t ldx, void *Y, in
 // Launch one column block (kb in {1, 2, 4, 8}) of the given storage type and
 // accumulation; part/cnt/cnt2 = nullptr uses the handle's scratch.  A single
 // column with launch mode 2 goes to the bulk-staged kernel.
-template <class VT, class Acc>
+template <class VT, class Acc, class AccL = Acc>
 cudaError_t spmv_block(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy, int kb,
                        int acc, int vec, void *part, int32_t *cnt, int32_t *cnt2, cudaStream_t s) {
     using namespace spmv_impl;
-    if (!part && kb == 1 && h->pipeline == 2 && h->bulk_grid > 0) return bulk::run<VT, Acc>(h, X, ldx, Y, ldy, acc, s);
-    if (!part) return pick_k<VT, Acc>(h, X, ldx, Y, ldy, kb, acc, vec, s);
-    return pick_with<VT, Acc>(h, X, ldx, Y, ldy, kb, acc, vec, part, cnt, cnt2, s);
+    if constexpr (std::is_same<Acc, AccL>::value) {  // the bulk kernel has one accumulation for all rows
+        if (!part && kb == 1 && h->pipeline == 2 && h->bulk_grid > 0)
+            return bulk::run<VT, Acc>(h, X, ldx, Y, ldy, acc, s);
+    }
+    if (!part) return pick_k<VT, Acc, AccL>(h, X, ldx, Y, ldy, kb, acc, vec, s);
+    return pick_with<VT, Acc, AccL>(h, X, ldx, Y, ldy, kb, acc, vec, part, cnt, cnt2, s);
 }
 
 }  // namespace sell

@@ -24,6 +24,7 @@ SELL_BUILD_PERMUTE_COLS = 0x1
 SELL_SPMV_ACCUMULATE = 0x1
 SELL_SPMV_COMPENSATED = 0x2
 SELL_SPMV_HOST_IO = 0x4
+SELL_SPMV_COMPENSATED_LONG = 0x8
 
 DTYPE_NAMES = {SELL_F64: "f64", SELL_F32: "f32", SELL_BF16: "bf16"}
 VALUE_BYTES = {SELL_F64: 8, SELL_F32: 4, SELL_BF16: 2}

@@ -25,7 +25,11 @@ def _make_products(seed=0, n=24):
         dt = torch.float64 if store == sell.SELL_F64 else torch.float32
         X = torch.from_numpy(synth.block(A.ncols, k, seed=100 + i)).to(dt).cuda()
         Y = torch.full((A.nrows, k), float("nan"), dtype=dt, device="cuda")
-        fl = sell.SELL_SPMV_COMPENSATED if (store != sell.SELL_F64 and i % 4 == 1) else 0
+        fl = 0
+        if store != sell.SELL_F64 and i % 4 == 1:
+            fl = sell.SELL_SPMV_COMPENSATED
+        elif store != sell.SELL_F64 and i % 4 == 3:
+            fl = sell.SELL_SPMV_COMPENSATED_LONG
         prods.append((h, X, Y, fl))
     return prods
 
