@@ -22,6 +22,7 @@ Function -> paper passage:
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -39,50 +40,74 @@ _lib = None
 F32, BF16 = 1, 2
 
 
-def build(force: bool = False) -> str:
-    """Compile sell_oracle.c with gcc (OpenMP if available)."""
-    os.makedirs(_LIB_DIR, exist_ok=True)
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
-        return _LIB
+def compile_library(src: str, out: str) -> str:
+    """Compile a C oracle source into a shared library (OpenMP if available)."""
+    os.makedirs(os.path.dirname(out), exist_ok=True)
     base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-            "-fno-fast-math", _SRC, "-o", _LIB + ".tmp", "-lm"]
+            "-fno-fast-math", src, "-o", out + ".tmp", "-lm"]
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
                        capture_output=True)
     except subprocess.CalledProcessError:
         subprocess.run(base, check=True, capture_output=True)
-    os.replace(_LIB + ".tmp", _LIB)
-    return _LIB
+    os.replace(out + ".tmp", out)
+    return out
+
+
+def build(force: bool = False) -> str:
+    """Compile sell_oracle.c with gcc (OpenMP if available)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    return compile_library(_SRC, _LIB)
+
+
+def _bind(path: str):
+    lib = ctypes.CDLL(path)
+    p = ctypes.c_void_p
+    i64, i32, f64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    sig = {
+        "orc_csr_spmv": (None, [i64, p, p, p, p, p, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "orc_csr_spmv_rows": (None, [p, p, p, p, p, i64, p, p]),
+        "orc_csr_spmmv": (None, [i64, p, p, p, i32, p, i64, p, i64, ctypes.c_int]),
+        "orc_csr_absdot": (None, [i64, p, p, p, p, p]),
+        "orc_sell_plan": (ctypes.c_int, [i64, p, i32, i64, p, p, p, p]),
+        "orc_sell_fill": (ctypes.c_int, [i64, i64, p, p, p, i32, p, p, p, p, ctypes.c_int, p, p, p]),
+        "orc_sell_spmv": (None, [i64, i32, p, p, p, p, p, p, p, ctypes.c_int, ctypes.c_int]),
+        "orc_beta": (f64, [i64, i64, i32, p]),
+        "orc_zeta": (f64, [i64, p]),
+        "orc_round": (None, [i64, p, ctypes.c_int, p]),
+        "orc_bf16_to_f64": (None, [i64, p, p]),
+        "orc_max_threads": (ctypes.c_int, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
 
 
 def _load():
     global _lib
     with _lock:
-        if _lib is not None:
-            return _lib
-        lib = ctypes.CDLL(build())
-        p = ctypes.c_void_p
-        i64, i32, f64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
-        sig = {
-            "orc_csr_spmv": (None, [i64, p, p, p, p, p, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
-            "orc_csr_spmv_rows": (None, [p, p, p, p, p, i64, p, p]),
-            "orc_csr_spmmv": (None, [i64, p, p, p, i32, p, i64, p, i64, ctypes.c_int]),
-            "orc_csr_absdot": (None, [i64, p, p, p, p, p]),
-            "orc_sell_plan": (ctypes.c_int, [i64, p, i32, i64, p, p, p, p]),
-            "orc_sell_fill": (ctypes.c_int, [i64, i64, p, p, p, i32, p, p, p, p, ctypes.c_int, p, p, p]),
-            "orc_sell_spmv": (None, [i64, i32, p, p, p, p, p, p, p, ctypes.c_int, ctypes.c_int]),
-            "orc_beta": (f64, [i64, i64, i32, p]),
-            "orc_zeta": (f64, [i64, p]),
-            "orc_round": (None, [i64, p, ctypes.c_int, p]),
-            "orc_bf16_to_f64": (None, [i64, p, p]),
-            "orc_max_threads": (ctypes.c_int, []),
-        }
-        for name, (res, args) in sig.items():
-            fn = getattr(lib, name)
-            fn.restype = res
-            fn.argtypes = args
-        _lib = lib
-        return lib
+        if _lib is None:
+            _lib = _bind(build())
+        return _lib
+
+
+@contextlib.contextmanager
+def substituted_library(path: str):
+    """Run this module's functions on another build of the C source for the
+    duration of the block.  Used only by the mutation tests, which plant one
+    mistake in a copy of sell_oracle.c and check that a pin catches it."""
+    global _lib
+    lib = _bind(path)
+    with _lock:
+        saved, _lib = _lib, lib
+    try:
+        yield
+    finally:
+        with _lock:
+            _lib = saved
 
 
 def _ptr(a: np.ndarray):

@@ -104,6 +104,17 @@ def test_csr_rows_matches_full_product_and_absdot():
     assert np.allclose(ab, (np.abs(d) @ np.abs(x))[rows], rtol=1e-13)
 
 
+def test_absdot_is_dense_abs_product():
+    """sum_j |a_ij x_j| (the scale of every tolerance) against |A| |x| computed
+    densely; with small integers both are exact."""
+    rng = np.random.default_rng(13)
+    d = rng.integers(-9, 10, (30, 21)).astype(np.float64)
+    d[rng.random(d.shape) < 0.5] = 0.0
+    A = synth.from_dense(d)
+    x = rng.integers(-6, 7, 21).astype(np.float64)
+    assert np.array_equal(oracle.csr_absdot(A, x), np.abs(d) @ np.abs(x))
+
+
 def test_spmmv_columns_are_independent_spmv():
     A = synth.random_csr(50, 40, density=0.2, seed=9)
     X = synth.block(40, 5, seed=1)
@@ -232,7 +243,7 @@ def test_global_sort_minimises_storage():
     """sigma >= N (pJDS): after a global descending sort each chunk's width is
     its first row, so stored = C * sum of every C-th sorted length, the least
     storage over all row orders; every smaller scope stores at least as much."""
-    A = synth.lognormal(4000, seed=8)
+    A = synth.lognormal(4001, seed=8)  # N not a multiple of C: a partial last chunk
     C = 32
     srt = np.sort(A.row_lengths())[::-1]
     FN = oracle.sell_build(A, C, A.nrows)
@@ -361,6 +372,8 @@ def test_round_bf16_is_nearest():
     """Brute force: the rounded value is the nearest of its two bf16 neighbours."""
     rng = np.random.default_rng(5)
     a = rng.standard_normal(20000) * 10.0 ** rng.integers(-30, 30, 20000)
+    # and the subnormal range, 2^-133 (smallest subnormal) up to 2^-126
+    a = np.concatenate([a, rng.uniform(-1, 1, 5000) * 2.0 ** rng.integers(-135, -125, 5000)])
     r = oracle.round_values(a, oracle.BF16).astype(np.int64)
     v = oracle.bf16_to_f64(r.astype(np.uint16))
     up = oracle.bf16_to_f64(((r & 0x7FFF) + 1 | (r & 0x8000)).astype(np.uint16))
