@@ -20,6 +20,7 @@
 #include <map>
 #include <new>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "sell_rowdot.cuh"
@@ -65,9 +66,8 @@ struct LaunchParams {
 
 // One block per work unit, long-row units first in the grid so that they
 // start early (the same shape as the single-product kernel).
-template <class VT, int K, class Acc, class AccL = Acc>
-__global__ void __launch_bounds__(kTileRows)
-k_batch(const __grid_constant__ LaunchParams lp) {
+template <class VT, int K, class Acc, class AccL>
+__device__ __forceinline__ void batch_unit(const LaunchParams &lp) {
     using XT = typename XType<VT>::T;
     constexpr int U = K >= 4 ? 2 : 4;
     const uint64_t pol = l2_evict_first_policy();
@@ -98,13 +98,37 @@ k_batch(const __grid_constant__ LaunchParams lp) {
                                      P.vec != 0, pol);
 }
 
+// The kernel holds both the long-row path (segment folds) and the short-row
+// path.  Left alone, ptxas gives the one- and two-vector variants 60-64
+// registers (4 blocks of 256 threads per SM, half the SM's warps) for the
+// sake of the long-row path, although the short rows carry most of the work.
+// Their entry point therefore asks for 6 resident blocks (5 for bfloat16 and
+// for two vectors), which fits them in 40-48 registers with no spills (ptxas
+// -v).  Wider blocks need their registers for the K accumulators and keep the
+// allocation ptxas picks without a bound (64-76).
+template <class VT, int K>
+constexpr int narrow_min_blocks() {
+    return K == 1 && !std::is_same<VT, __nv_bfloat16>::value ? 6 : 5;
+}
+
+template <class VT, int K, class Acc, class AccL = Acc>
+__global__ void __launch_bounds__(kTileRows, (narrow_min_blocks<VT, K>()))
+k_batch_narrow(const __grid_constant__ LaunchParams lp) {
+    batch_unit<VT, K, Acc, AccL>(lp);
+}
+
+template <class VT, int K, class Acc, class AccL = Acc>
+__global__ void __launch_bounds__(kTileRows) k_batch(const __grid_constant__ LaunchParams lp) {
+    batch_unit<VT, K, Acc, AccL>(lp);
+}
+
 using KernelFn = void (*)(const LaunchParams);
 
 template <class VT, class Acc, class AccL = Acc>
 KernelFn kernel_for_k(int kb) {
     switch (kb) {
-        case 1: return k_batch<VT, 1, Acc, AccL>;
-        case 2: return k_batch<VT, 2, Acc, AccL>;
+        case 1: return k_batch_narrow<VT, 1, Acc, AccL>;
+        case 2: return k_batch_narrow<VT, 2, Acc, AccL>;
         case 4: return k_batch<VT, 4, Acc, AccL>;
         default: return k_batch<VT, 8, Acc, AccL>;
     }

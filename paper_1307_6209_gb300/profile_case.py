@@ -8,6 +8,13 @@ sigma) and storage type, fixes the launch, runs `--warmup` untimed and
 `--reps` timed products on one stream (CUDA events) and prints one JSON line
 with the kernel's average time, GF/s and algorithmic GB/s.  Everything runs
 through the C ABI; nothing is tuned.
+
+    python -m paper_1307_6209_gb300.profile_case --batch 64 --store f32 --C 32 --sigma 4096 --k 1
+
+runs a batch plan instead (sell_batch_create / sell_batch_run): `--batch`
+matrices with rows uniform in [1000, 200000] (seeded), even ones banded
+(bandwidth 64, 7-30 entries per row) and odd ones lognormal, all in the given
+(C, sigma) and storage type, each with its own k right-hand sides.
 """
 from __future__ import annotations
 
@@ -33,7 +40,10 @@ def main(argv=None):
     p.add_argument("--compensated", action="store_true")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--reps", type=int, default=5)
+    p.add_argument("--batch", type=int, default=0, help="run a batch plan of this many matrices")
     a = p.parse_args(argv)
+    if a.batch > 0:
+        return run_batch(a)
 
     if a.matrix == "stencil27":
         A = synth.stencil27_device(a.n, perturb=0.1, seed=0)
@@ -82,6 +92,54 @@ def main(argv=None):
                       "gflops": round(2.0 * inf.nnz * a.k / us / 1e3, 1),
                       "algorithmic_gbs": round(alg / us / 1e3, 1), "value_bytes": vb}))
     h.free()
+    return 0
+
+
+def run_batch(a):
+    import numpy as np
+    import torch
+
+    from . import model, sell, synth
+
+    st = {"f64": sell.SELL_F64, "f32": sell.SELL_F32, "bf16": sell.SELL_BF16}[a.store]
+    dt = torch.float64 if st == sell.SELL_F64 else torch.float32
+    vb = {sell.SELL_F64: 8, sell.SELL_F32: 4}.get(st, 2)
+    xb = 8 if st == sell.SELL_F64 else 4
+    s = torch.cuda.Stream()
+    sizes = np.random.default_rng(0).integers(1000, 200001, a.batch)
+    g = torch.Generator("cuda").manual_seed(0)
+    items, alg, nnz, stored = [], 0, 0, 0
+    for i, n in enumerate(sizes):
+        gen = synth.banded_device if i % 2 == 0 else synth.lognormal_device
+        A = gen(int(n), seed=i)
+        h = sell.sell_build(A, C=a.C, sigma=a.sigma, store_type=st, stream=s)
+        inf = h.info
+        shp_x = (inf.ncols,) if a.k == 1 else (inf.ncols, a.k)
+        shp_y = (inf.nrows,) if a.k == 1 else (inf.nrows, a.k)
+        items.append((h, torch.rand(shp_x, dtype=dt, device="cuda", generator=g) * 2 - 1,
+                      torch.empty(shp_y, dtype=dt, device="cuda"), 0))
+        alg += model.algorithmic_bytes(inf.nrows, inf.ncols, inf.nnz, inf.nchunks, a.C, vb, xb, inf.has_perm, k=a.k)
+        nnz += inf.nnz
+        stored += inf.stored
+        del A
+    plan = sell.sell_batch_create(items, stream=s)
+    for _ in range(a.warmup):
+        plan.run(stream=s)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.reps)]
+    for e0, e1 in ev:
+        e0.record(s)
+        plan.run(stream=s)
+        e1.record(s)
+    torch.cuda.synchronize()
+    us = sum(e0.elapsed_time(e1) for e0, e1 in ev) * 1e3 / a.reps
+    print(json.dumps({"batch": a.batch, "rows": int(sizes.sum()), "nnz": nnz, "stored": stored,
+                      "beta": round(nnz / max(stored, 1), 6), "store": a.store, "C": a.C, "sigma": a.sigma,
+                      "k": a.k, "us": round(us, 3), "gflops": round(2.0 * nnz * a.k / us / 1e3, 1),
+                      "algorithmic_bytes": alg, "algorithmic_gbs": round(alg / us / 1e3, 1),
+                      "value_bytes": vb}))
+    plan.free()
+    for h, _, _, _ in items:
+        h.free()
     return 0
 
 

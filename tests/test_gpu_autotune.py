@@ -56,3 +56,12 @@ def test_profile_case_runs(capsys):
                               "--unroll", "8", "--reps", "2"]) == 0
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert line["nnz"] == (3 * 24 - 2) ** 3 and line["us"] > 0 and line["store"] == "bf16"
+
+
+def test_profile_case_batch_runs(capsys):
+    from paper_1307_6209_gb300 import profile_case
+    assert profile_case.main(["--batch", "4", "--store", "f32", "--C", "32", "--sigma", "256", "--k", "4",
+                              "--reps", "2"]) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["batch"] == 4 and line["k"] == 4 and line["us"] > 0
+    assert 0 < line["beta"] <= 1 and line["nnz"] <= line["stored"]
