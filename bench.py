@@ -448,15 +448,18 @@ def stencil_section(sell, model, stream, peak, fma_tf, n=200):
 
 
 def _time_graph(g, stream, reps):
+    """Average time of one replay; the replays run on `stream`, where the
+    events are recorded (a graph replays on the current stream)."""
     import torch
-    g.replay()
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for _ in range(reps):
+    with torch.cuda.stream(stream):
         g.replay()
-    b.record(stream)
-    b.synchronize()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            g.replay()
+        b.record(stream)
+        b.synchronize()
     return a.elapsed_time(b) * 1e-3 / reps
 
 
