@@ -117,6 +117,10 @@ MUTANTS = [
      "orc_round_to(in[i], to == 1 ? 24 : 7);",
      [(pins.test_round_bf16_hand_derived, dict(value=1.0 + 2 ** -8 + 2 ** -30, bits=0x3F81)),
       (pins.test_round_bf16_is_nearest, {})]),
+    ("bfloat16 decoding: bits shifted one place too few",
+     "uint32_t bits = (uint32_t)in[i] << 16;",
+     "uint32_t bits = (uint32_t)in[i] << 15;",
+     [(pins.test_round_bf16_is_nearest, {})]),
     ("rounding: subnormal spacing one binade too fine",
      "if (E < -126) E = -126;",
      "if (E < -127) E = -127;",
