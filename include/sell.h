@@ -61,7 +61,9 @@ typedef enum {
     SELL_EINVAL = 1,       /* bad argument or malformed CRS input */
     SELL_ENOMEM = 2,       /* an allocation failed; nothing leaked */
     SELL_ECUDA = 3,        /* a CUDA runtime call failed (message kept) */
-    SELL_EBOUNDS = 4,      /* a kernel's own bounds check fired */
+    SELL_EBOUNDS = 4,      /* reserved for kernel-side bounds checks; no call
+                              of this version returns it (sizes and indices
+                              are validated on the host before a launch) */
     SELL_ETIMEOUT = 5,     /* a bounded device-side wait gave up */
     SELL_EUNSUPPORTED = 6  /* valid request this build does not support */
 } sell_status;
