@@ -380,7 +380,9 @@ SELL_API sell_status sell_server_submit(sell_server_t srv, int32_t mid, const vo
 /* Block until request id has completed (or timeout_s passed: SELL_ETIMEOUT)
  * and fill *info (may be NULL).  A request with a host Y is forgotten after
  * its wait; a device-result request stays until sell_server_release.
- * Errors: SELL_EINVAL (unknown id), SELL_ETIMEOUT, the batch's error. */
+ * Errors: SELL_EINVAL (unknown id, or a request that another thread delivered
+ * with sell_server_next or released while this call waited), SELL_ETIMEOUT,
+ * the batch's error. */
 SELL_API sell_status sell_server_wait(sell_server_t srv, uint64_t id, double timeout_s, sell_request_info *info);
 
 /* Deliver the next completed request not yet delivered by a wait, in
@@ -399,7 +401,8 @@ SELL_API sell_status sell_server_stats(sell_server_t srv, sell_server_stats_t *s
 
 /* Finish every queued and running request, stop the scheduler and free the
  * server (NULL accepted).  Device results not yet released are dropped first
- * (their memory goes with the server). */
+ * (their memory goes with the server).  No other call on the server may run
+ * at the same time or follow it. */
 SELL_API sell_status sell_server_destroy(sell_server_t srv);
 
 /* ------------------------------------------------------------ measuring */

@@ -497,17 +497,20 @@ sell_status sell_server_submit(sell_server_t S, int32_t mid, const void *X, int3
 sell_status sell_server_wait(sell_server_t S, uint64_t id, double timeout_s, sell_request_info *info) {
     if (!S) return fail(SELL_EINVAL, "sell_server_wait: NULL server");
     std::unique_lock<std::mutex> lk(S->mu);
-    auto it = S->reqs.find(id);
-    if (it == S->reqs.end()) return fail(SELL_EINVAL, "sell_server_wait: unknown request");
-    Req *r = it->second;
     const auto until = std::chrono::steady_clock::now() +
                        std::chrono::duration_cast<std::chrono::steady_clock::duration>(
                            std::chrono::duration<double>(timeout_s > 0 ? timeout_s : 0));
-    while (r->state != kDone) {
-        if (S->cv_done.wait_until(lk, until) == std::cv_status::timeout && r->state != kDone)
-            return fail(SELL_ETIMEOUT, "sell_server_wait: timed out");
+    for (bool timed_out = false;;) {
+        // looked up again after every wake-up: while this thread slept, another
+        // one may have delivered the request (sell_server_next) or released it,
+        // and the request may no longer exist
+        auto it = S->reqs.find(id);
+        if (it == S->reqs.end())
+            return fail(SELL_EINVAL, "sell_server_wait: unknown request (or delivered to another caller)");
+        if (it->second->state == kDone) return collect(S, it, info);
+        if (timed_out) return fail(SELL_ETIMEOUT, "sell_server_wait: timed out");
+        timed_out = S->cv_done.wait_until(lk, until) == std::cv_status::timeout;
     }
-    return collect(S, it, info);
 }
 
 sell_status sell_server_next(sell_server_t S, double timeout_s, uint64_t *id, sell_request_info *info) {

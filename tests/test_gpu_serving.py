@@ -225,3 +225,43 @@ def test_size_ratio_batches_keep_results_and_order():
     for r in reqs:
         assert r.Y.numpy().tobytes() == _alone(mats[r.mid], r.X).numpy().tobytes()
     assert reqs[0].t_launch <= min(r.t_launch for r in reqs[1:])
+
+
+def test_wait_and_next_racing_for_one_request():
+    """One thread waits on a request while another takes the next completed
+    request: exactly one of the two delivers it, and the other gets an error
+    (never a request that was freed while it slept)."""
+    import torch
+    from paper_1307_6209_gb300 import sell
+    A = synth.lognormal_device(20000, seed=3, cap=500)
+    h = sell.sell_build(A, C=32, sigma=20000)
+    srv = sell.sell_server_create([h], budget_bytes=1 << 30, max_batch=4, streams=1)
+    try:
+        for _ in range(8):
+            X = torch.rand(A.ncols, dtype=torch.float64).pin_memory()
+            Y = torch.empty(A.nrows, dtype=torch.float64).pin_memory()
+            rid = sell.sell_server_submit(srv, 0, X.data_ptr(), 1, Y.data_ptr())
+            out = {}
+
+            def waiter():
+                try:
+                    sell.sell_server_wait(srv, rid, 10.0)
+                    out["wait"] = "ok"
+                except sell.SellError as e:
+                    out["wait"] = e.status
+
+            t = threading.Thread(target=waiter)
+            t.start()
+            try:
+                out["next"] = sell.sell_server_next(srv, 1.0)[0]
+            except sell.SellError as e:
+                out["next"] = e.status
+            t.join(20)
+            assert not t.is_alive()
+            if out["wait"] == "ok":
+                assert out["next"] == sell.SELL_ETIMEOUT
+            else:
+                assert out["wait"] == sell.SELL_EINVAL and out["next"] == rid
+    finally:
+        sell.sell_server_destroy(srv)
+        h.free()
