@@ -90,7 +90,8 @@ def tune(A, store_type: int = sell.SELL_F64, k: int = 1, Cs=(32, 64, 128), sigma
 
     stream = stream or torch.cuda.current_stream()
     nrows = int(A.nrows)
-    sigmas = sigmas or (1, 256, 4096, max(nrows, 1))
+    # sigma = N may coincide with a fixed point of the sweep (N = 256, 4096)
+    sigmas = tuple(dict.fromkeys(sigmas or (1, 256, 4096, max(nrows, 1))))
     dt = torch.float64 if store_type == sell.SELL_F64 else torch.float32
     X = torch.rand((int(A.ncols), k), dtype=dt, device="cuda") * 2 - 1
     Y = torch.empty((nrows, k), dtype=dt, device="cuda")
