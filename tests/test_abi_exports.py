@@ -72,3 +72,26 @@ int main(void){
                      ctypes.sizeof(sell.sell_info_t), ctypes.sizeof(sell.sell_batch_item)]
     assert offs == [sell.sell_csr.val_type.offset, sell.sell_opts.flags.offset,
                     sell.sell_info_t.beta.offset, sell.sell_batch_item.k.offset]
+
+
+def test_every_struct_field_matches_header(lib_path, tmp_path):
+    """Every field of every ctypes mirror against offsetof() in C, plus the
+    sizes: a layout slip would pass wrong arguments silently."""
+    from paper_1307_6209_gb300 import sell
+    mirrors = [sell.sell_csr, sell.sell_opts, sell.sell_info_t, sell.sell_batch_item, sell.sell_server_opts,
+               sell.sell_request_info, sell.sell_server_stats_t]
+    body, want = [], []
+    for m in mirrors:
+        body.append(f'printf("%zu\\n", sizeof({m.__name__}));')
+        want.append(ctypes.sizeof(m))
+        for name, _ in m._fields_:
+            body.append(f'printf("%zu\\n", offsetof({m.__name__}, {name}));')
+            want.append(getattr(m, name).offset)
+    prog = "#include <stdio.h>\n#include <stddef.h>\n#include \"sell.h\"\nint main(void){\n" + \
+        "\n".join(body) + "\nreturn 0;}\n"
+    c, exe = tmp_path / "fields.c", tmp_path / "fields"
+    c.write_text(prog)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(c), "-o",
+                    str(exe)], check=True)
+    got = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()))
+    assert got == want
