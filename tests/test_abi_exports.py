@@ -95,3 +95,47 @@ def test_every_struct_field_matches_header(lib_path, tmp_path):
                     str(exe)], check=True)
     got = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()))
     assert got == want
+
+
+_HANDLES = {"sell_handle", "sell_batch_plan", "sell_server_t", "sell_alloc_fn", "sell_free_fn"}
+_SCALARS = {"int32_t": ("i", 4), "sell_status": ("i", 4), "int64_t": ("i", 8), "uint32_t": ("u", 4),
+            "uint64_t": ("u", 8), "size_t": ("u", 8), "double": ("f", 8)}
+
+
+def _c_kind(t):
+    t = " ".join(t.replace("const", " ").split())
+    if "*" in t or t in _HANDLES:
+        return ("p", 8)
+    return _SCALARS[t]
+
+
+def _ctypes_kind(t):
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or issubclass(t, (ctypes._Pointer, ctypes._CFuncPtr)):
+        return ("p", 8)
+    if t is ctypes.c_double:
+        return ("f", 8)
+    return ("i" if t(-1).value < 0 else "u", ctypes.sizeof(t))
+
+
+def test_binding_argument_types_match_prototypes():
+    """Each ctypes signature of the binding against the prototype in
+    include/sell.h: the same number of arguments, each of the same kind and
+    width (a 32-bit integer where the C side reads 64 bits would corrupt the
+    call silently), and pointers to the struct mirrors of the named types."""
+    from paper_1307_6209_gb300 import sell
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "sell.h")).read(), flags=re.S)
+    protos = {m.group(2): (m.group(1), m.group(3)) for m in
+              re.finditer(r"SELL_API\s+([\w\s\*]+?)\b(sell_\w+)\s*\(([^;]*?)\)\s*;", src, flags=re.S)}
+    assert set(protos) == set(sell.SIGNATURES)
+    for name, (ret, params) in protos.items():
+        res, args = sell.SIGNATURES[name]
+        assert _c_kind(ret) == _ctypes_kind(res), name
+        ps = [] if params.strip() == "void" else [p.strip() for p in params.split(",")]
+        assert len(ps) == len(args), name
+        for p, a in zip(ps, args):
+            ctype = re.sub(r"\b\w+\s*$", "", p).strip()  # drop the parameter name
+            assert _c_kind(ctype) == _ctypes_kind(a), f"{name}: {p}"
+            base = " ".join(ctype.replace("const", " ").replace("*", " ").split())
+            if ctype.count("*") == 1 and hasattr(sell, base) and isinstance(getattr(sell, base), type) \
+                    and issubclass(getattr(sell, base), ctypes.Structure):
+                assert issubclass(a, ctypes._Pointer) and a._type_ is getattr(sell, base), f"{name}: {p}"
