@@ -73,16 +73,17 @@ def _worker(rank, world, port, results):
         dist.destroy_process_group()
 
 
-def test_two_ranks_gloo():
+@pytest.mark.parametrize("world", [2, 3])
+def test_ranks_gloo(world):
     import torch.multiprocessing as mp
-    world = 2
     port = _free_port()
     with mp.Manager() as m:
         results = m.dict()
         mp.spawn(_worker, args=(world, port, results), nprocs=world, join=True)
         res = dict(results)
     for r in range(world):
-        assert res[r]["tp"] == pytest.approx(200.0)
+        # units 100, 200, ... over the slowest rank's 0.5 + (world - 1) seconds
+        assert res[r]["tp"] == pytest.approx(100.0 * world * (world + 1) / 2 / (0.5 + world - 1))
         assert res[r]["pieces"], f"rank {r}: shard format is not a piece of the global format"
         assert res[r]["y_equal"], f"rank {r}: sharded product differs"
     b = res[0]["bounds"]
@@ -97,3 +98,18 @@ def test_shard_rows_alignment():
         step = np.lcm(max(1, min(sigma, n) if n else 1), C)
         assert all(a <= c for (a, c) in b)
         assert all(a % step == 0 or a == n for a, _ in b)
+
+
+def test_shard_rows_balances_nonzeros():
+    """With the row offsets given, every shard holds its share of the nonzeros
+    to within one block of whole windows and chunks."""
+    from paper_1307_6209_gb300 import dist as sdist
+    from paper_1307_6209_gb300 import synth
+    A = synth.lognormal(20000, seed=6, cap=1000)
+    for sigma, C, w in [(256, 32, 4), (1, 32, 5), (4096, 64, 3)]:
+        b = sdist.shard_rows(A.nrows, sigma, C, w, rpt=A.rpt)
+        step = int(np.lcm(min(sigma, A.nrows), C))
+        blk = max(int(A.rpt[min(i + step, A.nrows)] - A.rpt[i]) for i in range(0, A.nrows, step))
+        for k, (r0, r1) in enumerate(b):
+            assert r0 % step == 0 and (r1 % step == 0 or r1 == A.nrows)
+            assert abs(int(A.rpt[r1]) - A.nnz * (k + 1) / w) <= blk
