@@ -28,6 +28,10 @@
  *   orc_round : f32 leg equals the C cast; bf16 leg checked on hand-derived
  *       ties, overflow and subnormal boundaries.
  *   orc_zeta : closed form on constant and two-valued length profiles.
+ * The pins are themselves tested: tests/test_oracle_mutants.py plants one
+ * plausible mistake at a time in a copy of this file and checks that a named
+ * pin fails; tests/test_oracle_properties.py checks the same facts on random
+ * small matrices (hypothesis).
  */
 #include <math.h>
 #include <stdint.h>
