@@ -139,3 +139,37 @@ def test_binding_argument_types_match_prototypes():
             if ctype.count("*") == 1 and hasattr(sell, base) and isinstance(getattr(sell, base), type) \
                     and issubclass(getattr(sell, base), ctypes.Structure):
                 assert issubclass(a, ctypes._Pointer) and a._type_ is getattr(sell, base), f"{name}: {p}"
+
+
+def test_c_program_links_and_calls_host_only_entry_points(lib_path, tmp_path):
+    """A C program that takes the address of every declared entry point links
+    against the library, and runs the calls that need no GPU: error strings,
+    argument validation before any device work, the allocator hook."""
+    names = sorted(_declared())
+    prog = ["#include <stdio.h>", "#include <string.h>", '#include "sell.h"',
+            "static void *fake_alloc(size_t n, void *c, void *s) { (void)n; (void)c; (void)s; return 0; }",
+            "static void fake_free(void *p, void *c, void *s) { (void)p; (void)c; (void)s; }",
+            "int main(void) {", "  void *fns[] = {"]
+    prog += [f"    (void *)&{n}," for n in names]
+    prog += ["  };",
+             "  int missing = 0;",
+             "  for (size_t i = 0; i < sizeof fns / sizeof fns[0]; ++i) missing += fns[i] == 0;",
+             "  if (missing) return 2;",
+             '  if (strcmp(sell_strerror(SELL_EINVAL), "invalid argument")) return 3;',
+             "  if (sell_build(NULL, NULL, NULL, NULL) != SELL_EINVAL) return 4;",
+             "  if (sell_spmv(NULL, NULL, NULL, 0, NULL) != SELL_EINVAL) return 5;",
+             "  if (strlen(sell_last_error()) == 0) return 6;",
+             "  if (sell_set_allocator(fake_alloc, NULL, NULL) != SELL_EINVAL) return 7;",
+             "  if (sell_set_allocator(fake_alloc, fake_free, NULL) != SELL_OK) return 8;",
+             "  if (sell_set_allocator(NULL, NULL, NULL) != SELL_OK) return 9;",
+             "  if (sell_free(NULL) != SELL_OK || sell_server_destroy(NULL) != SELL_OK) return 10;",
+             '  printf("ok %zu\\n", sizeof fns / sizeof fns[0]);',
+             "  return 0;", "}"]
+    c, exe = tmp_path / "use.c", tmp_path / "use"
+    c.write_text("\n".join(prog) + "\n")
+    libdir = os.path.dirname(lib_path)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(c),
+                    "-L", libdir, "-lsellcs", f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    assert r.stdout.strip() == f"ok {len(names)}"
