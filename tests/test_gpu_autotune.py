@@ -3,7 +3,6 @@ returns one of them, caches it by matrix signature, and the tuned handle
 gives the same bits as any other format (the choice is a speed choice only)."""
 import json
 
-import numpy as np
 import pytest
 
 from paper_1307_6209_gb300 import synth

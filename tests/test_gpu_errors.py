@@ -1,6 +1,5 @@
 """Failure handling through the C ABI, made on the host: malformed CRS input,
 bad options, and an allocator that fails on demand (no GPU fault involved)."""
-import ctypes
 
 import numpy as np
 import pytest
