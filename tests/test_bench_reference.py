@@ -37,3 +37,15 @@ def test_rank0_prints_one_line_with_the_contract_keys():
 def test_other_ranks_exit_without_work():
     r = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}, "--steps", "2", "--warmup", "3", "--gpus", "2")
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_cpu_baseline_leg_reports_the_oracle():
+    """The cpu_baseline object of our arm's line: the oracle's CRS SpMV timed
+    on the host cores, with its sample and schedule stated."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1307_6209_gb300 import synth
+    A = synth.lognormal(20000, seed=1)
+    cb = bench.cpu_baseline(A, synth.vector(A.ncols, seed=0), target_s=0.2)
+    assert cb["kind"] == "oracle" and cb["unit"] == "GF/s" and cb["value"] > 0 and cb["cores"] >= 1
+    assert f"({A.nnz} nnz)" in cb["sample"] and "GUIDED,1" in cb["sample"]  # zeta >= 0.4 here
