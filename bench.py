@@ -1,26 +1,30 @@
 #!/usr/bin/env python
 """SELL-C-sigma SpMV benchmark (GB300, sm_103a).
 
-Default workload: random square matrix, N = 2,000,000 rows, row lengths
-lognormal (mean 16, log-sd 1.2, capped at 2000), uniform distinct columns,
-N(0,1) binary64 values, x ~ U[-1, 1] (seed 0).  The autotuner builds the
-format for every point of the sweep C in {32, 64, 128} x sigma in
-{1, 256, 4096, N}, then picks the launch shape; the headline step is one
-binary64 SpMV y = A x with the tuned choice.  The line also reports SpMMV,
-binary32/bfloat16 storage, the end-to-end rate through host buffers, the
-co-bounds (HBM read bandwidth, L2 random-gather rate, FP64 FMA rate), and the
-27-point stencil on 200^3 in binary64/binary32/bfloat16.
+Headline workload: the 27-point stencil on a 200^3 grid (N = 8,000,000 rows,
+213,847,192 nonzeros), binary64 values 26 / -1 times 1 + 0.1 U(-1, 1), generated
+on the device; x ~ U[-1, 1] (seed 0).  It is the largest configuration that
+fits one GPU.  The autotuner picks C, sigma and the launch shape; a step is
+one binary64 SpMV y = A x with the tuned choice.
+
+The line also reports, for the same matrix, binary32 and bfloat16 storage
+("FP64 vs mixed"), SpMMV and the end-to-end rate through host buffers; the
+co-bounds (HBM read bandwidth, L2 random-gather rate, FP64 FMA rate); the
+lognormal N = 2,000,000 matrix with its C x sigma sweep; the 5-point
+Laplacian; the pathological shapes of Sec. 5.2; the 512-matrix batch; the
+64-matrix serving run; and it ends with a compact summary of every figure.
 
 One JSON line is printed by rank 0.  Under torchrun every rank runs its own
 replica of the workload on its own GPU (independent problems, no data-path
 collective: weak scaling); the step time is the maximum over ranks.
 
 --impl reference runs the CPU oracle (CRS SpMV in binary64, OpenMP on the
-host cores) on a bounded row sample per step instead.
+host cores) on a bounded row sample of the same workload per step instead.
 """
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -49,11 +53,11 @@ KERNEL_SOURCES = ["paper_1307_6209_gb300/csrc/sell_spmv_impl.cuh", "paper_1307_6
 def parse_args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10000)
-    p.add_argument("--warmup", type=int, default=100)
+    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["lognormal", "stencil27", "laplace"], default="lognormal")
-    p.add_argument("--n", type=int, default=None, help="rows (lognormal) or grid edge (stencils)")
+    p.add_argument("--workload", choices=["stencil27", "lognormal", "laplace"], default="stencil27")
+    p.add_argument("--n", type=int, default=None, help="grid edge (stencils) or rows (lognormal)")
     p.add_argument("--C", type=int, default=None)
     p.add_argument("--sigma", type=int, default=None)
     p.add_argument("--block", type=int, default=None, help="fix the launch block instead of tuning it")
@@ -61,30 +65,46 @@ def parse_args():
     p.add_argument("--pipeline", type=int, default=None, help="fix the launch mode (0, 1, 2) instead of tuning it")
     p.add_argument("--no-sweep", action="store_true")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    p.add_argument("--no-extras", action="store_true", help="skip SpMMV / mixed / e2e extras")
+    p.add_argument("--no-extras", action="store_true", help="skip every section but the headline")
     return p.parse_args()
 
 
-# ------------------------------------------------------------------ workload
-def make_workload(args):
+# ------------------------------------------------------------------ workloads
+def workload(args):
+    """The workload's description, tuning grid and generators: `device()`
+    returns the CSR on the GPU (torch arrays), `host(rows)` the CSR (or its
+    first `rows` rows) in numpy."""
     from paper_1307_6209_gb300 import synth
+    if args.workload == "stencil27":
+        n = args.n or 200
+        N, nnz = n ** 3, (3 * n - 2) ** 3
+        return {"name": "stencil27", "nrows": N, "nnz": nnz,
+                "desc": f"27-point stencil on a {n}^3 grid (N={N}, nnz={nnz}), FP64 values 26/-1 times "
+                        f"1+0.1*U(-1,1), x ~ U[-1,1] seed 0",
+                "grid": [(32, 1), (32, 4096), (64, 1), (128, 1)],
+                "device": lambda: synth.stencil27_device(n, perturb=0.1, seed=0),
+                "host": lambda rows=None: synth.stencil27(n, perturb=0.1, seed=0, rows=rows)}
     if args.workload == "lognormal":
         n = args.n or 2_000_000
-        A = synth.lognormal(n, mean=16.0, sigma_ln=1.2, cap=2000, seed=0)
-        desc = f"lognormal random N={n} (row length mean 16, log-sd 1.2, cap 2000), FP64"
-        grid = [(C, s) for C in (32, 64, 128) for s in (1, 256, 4096, n)]
-    elif args.workload == "stencil27":
-        n = args.n or 200
-        A = synth.stencil27(n, perturb=0.1, seed=0)
-        desc = f"27-point stencil on a {n}^3 grid, FP64"
-        grid = [(32, 1), (32, 4096), (64, 1), (128, 1)]
-    else:
-        n = args.n or 64
-        A = synth.laplace2d(n)
-        desc = f"5-point Laplacian on a {n}x{n} grid, FP64"
-        grid = [(32, 1)]
-    x = synth.vector(A.ncols, seed=0)
-    return A, x, desc, grid
+        return {"name": "lognormal", "nrows": n, "nnz": None,
+                "desc": f"lognormal random N={n} (row length mean 16, log-sd 1.2, cap 2000), FP64",
+                "grid": [(C, s) for C in (32, 64, 128) for s in (1, 256, 4096, n)],
+                "device": None,
+                "host": lambda rows=None: synth.lognormal(n, mean=16.0, sigma_ln=1.2, cap=2000, seed=0)}
+    n = args.n or 64
+    return {"name": "laplace", "nrows": n * n, "nnz": None,
+            "desc": f"5-point Laplacian on a {n}x{n} grid, FP64", "grid": [(32, 1)], "device": None,
+            "host": lambda rows=None: synth.laplace2d(n)}
+
+
+def to_device(A):
+    import torch
+    return type(A)(A.nrows, A.ncols, torch.from_numpy(A.rpt).cuda(), torch.from_numpy(A.col).cuda(),
+                   torch.from_numpy(A.val).cuda())
+
+
+def to_host(A):
+    return type(A)(A.nrows, A.ncols, A.rpt.cpu().numpy(), A.col.cpu().numpy(), A.val.cpu().numpy())
 
 
 def load_peaks():
@@ -132,7 +152,82 @@ def lookup_traffic(workload_key):
 
 
 # ------------------------------------------------------------------ clocks
-class ClockSampler:
+class NvmlClocks:
+    """The SM clock and the clock-event reasons, polled about once per
+    millisecond through NVML (libnvidia-ml; read-only queries), so that even
+    a timed region of a few milliseconds carries samples of its own."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, cuda_index):
+        self.ok = False
+        self.samples = []
+        self.max_mhz = None
+        self._stop = threading.Event()
+        self._thread = None
+        try:
+            import torch
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return
+            dev = ctypes.c_void_p()
+            found = False
+            try:
+                uuid = "GPU-" + str(torch.cuda.get_device_properties(cuda_index).uuid)
+                found = lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(dev)) == 0
+            except Exception:
+                found = False
+            if not found and lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(cuda_index), ctypes.byref(dev)) != 0:
+                return
+            self.lib, self.dev = lib, dev
+            mx = ctypes.c_uint()
+            if lib.nvmlDeviceGetMaxClockInfo(dev, 1, ctypes.byref(mx)) == 0:
+                self.max_mhz = float(mx.value)
+            self.reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons", None)
+            self.ok = True
+        except Exception:
+            self.ok = False
+
+    def start(self):
+        if self.ok:
+            self._thread = threading.Thread(target=self._run, daemon=True)
+            self._thread.start()
+        return self
+
+    def _run(self):
+        clk, rs = ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self._stop.is_set():
+            t = time.perf_counter()
+            if self.lib.nvmlDeviceGetClockInfo(self.dev, 1, ctypes.byref(clk)) == 0:
+                r = 0
+                if self.reasons_fn is not None and self.reasons_fn(self.dev, ctypes.byref(rs)) == 0:
+                    r = rs.value
+                self.samples.append((t, float(clk.value), r))
+            self._stop.wait(0.001)
+
+    def stop(self):
+        self._stop.set()
+        if self._thread:
+            self._thread.join(timeout=2)
+
+    def summary(self, t0, t1):
+        """Samples taken between perf_counter() times t0 and t1."""
+        if not self.ok:
+            return None
+        win = [s for s in self.samples if t0 <= s[0] <= t1]
+        if not win and self.samples:
+            win = [min(self.samples, key=lambda s: abs(s[0] - 0.5 * (t0 + t1)))]
+        if not win:
+            return None
+        reasons = sorted({nm for _, _, r in win for bit, nm in self.REASONS.items() if r & bit})
+        return {"sm_mhz": statistics.median(s[1] for s in win), "sm_max_mhz": self.max_mhz,
+                "reasons": reasons, "samples": len(win), "source": "nvml, ~1 ms polling"}
+
+
+class SmiClocks:
+    """nvidia-smi sampled every 100 ms over the whole run, summarised per
+    section (a window of wall-clock time named by the caller)."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -141,7 +236,7 @@ class ClockSampler:
         self.idx = gpu_index
         self.samples = []
         self.proc = None
-        self.thread = None
+        self.sections = []
 
     def start(self):
         try:
@@ -150,13 +245,16 @@ class ClockSampler:
                  "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
-            return
-        self.thread = threading.Thread(target=self._read, daemon=True)
-        self.thread.start()
+            return self
+        threading.Thread(target=self._read, daemon=True).start()
+        return self
 
     def _read(self):
         for ln in self.proc.stdout:
-            self.samples.append((time.time(), [v.strip() for v in ln.split(",")]))
+            self.samples.append((time.perf_counter(), [v.strip() for v in ln.split(",")]))
+
+    def section(self, name, t0, t1):
+        self.sections.append((name, t0, t1))
 
     def stop(self):
         if self.proc:
@@ -167,24 +265,21 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self, t0, t1):
-        win = [s for t, s in self.samples if t0 - 0.25 <= t <= t1 + 0.25]
-        if not win and self.samples:
-            mid = 0.5 * (t0 + t1)
-            win = [min(self.samples, key=lambda ts: abs(ts[0] - mid))[1]]
+        win = [s for t, s in self.samples if t0 <= t <= t1]
         if not win:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+            return {"samples": 0}
         sm = [float(s[1]) for s in win if s[1].replace(".", "").isdigit()]
         mx = [float(s[2]) for s in win if s[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = set()
-        for s in win:
-            for i, nm in enumerate(names):
-                if len(s) > 5 + i and s[5 + i].lower().startswith("active"):
-                    reasons.add(nm)
         pw = [float(s[3]) for s in win if s[3].replace(".", "").isdigit()]
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(win),
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({nm for s in win for i, nm in enumerate(names)
+                          if len(s) > 5 + i and s[5 + i].lower().startswith("active")})
+        return {"samples": len(win), "sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
                 "power_w_median": statistics.median(pw) if pw else None}
+
+    def by_section(self):
+        return {name: self.summary(t0, t1) for name, t0, t1 in self.sections}
 
 
 # ------------------------------------------------------------------ helpers
@@ -294,7 +389,7 @@ def measure_fp64_fma(sell, stream, iters=2000):
     return 2.0 * fmas / (a.elapsed_time(b) * 1e-3) / 1e12
 
 
-def cpu_baseline(A, x, target_s=10.0):
+def cpu_baseline(A, x, what, target_s=10.0):
     """The oracle's CRS SpMV (binary64, OpenMP on all host cores, STATIC or
     GUIDED,1 by the zeta heuristic of Sec. 5) timed on the full matrix."""
     import oracle
@@ -310,8 +405,8 @@ def cpu_baseline(A, x, target_s=10.0):
         oracle.csr_spmv(A, x, nthreads=nth, guided=guided)
     dt = (time.perf_counter() - t0) / reps
     return {"value": round(2.0 * A.nnz / dt / 1e9, 3), "unit": "GF/s", "cores": nth, "kind": "oracle",
-            "sample": f"full matrix ({A.nnz} nnz), {reps} calls, schedule "
-                      f"{'GUIDED,1' if guided else 'STATIC'} (zeta={zeta:.2f})"}
+            "sample": f"{what}: the full matrix ({A.nnz} nnz), {reps} calls of the binary64 CRS SpMV, "
+                      f"OpenMP {'GUIDED,1' if guided else 'STATIC'} (zeta={zeta:.2f})"}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -321,17 +416,35 @@ def run_reference(args):
         return 0
     import oracle
     from paper_1307_6209_gb300 import synth
-    A, x, desc, _ = make_workload(args)
+    W = workload(args)
     nth = os.cpu_count() or 1
-    zeta = oracle.zeta(A.row_lengths().astype(np.int32))
-    guided = zeta >= 0.4
-    t0 = time.perf_counter()
-    oracle.csr_spmv(A, x, nthreads=nth, guided=guided)
-    t_full = time.perf_counter() - t0
+    x = synth.vector(W["nrows"], seed=0)
     budget = 90.0  # seconds for warm-up + timed steps
-    frac = min(1.0, budget / max((args.steps + args.warmup) * t_full, 1e-9))
-    nrow = max(1, int(A.nrows * frac))
-    S = synth.CSR(nrow, A.ncols, A.rpt[:nrow + 1].copy(), A.col[:A.rpt[nrow]], A.val[:A.rpt[nrow]])
+    calls = args.steps + args.warmup
+    if W["name"] == "stencil27":
+        # rows of the stencil are generated directly; a probe prefix sizes the sample
+        probe = synth.stencil27(round(W["nrows"] ** (1 / 3)), perturb=0.1, seed=0, rows=min(W["nrows"], 200_000))
+        zeta = oracle.zeta(probe.row_lengths().astype(np.int32))
+        guided = zeta >= 0.4
+        oracle.csr_spmv(probe, x, nthreads=nth, guided=guided)
+        t0 = time.perf_counter()
+        for _ in range(3):
+            oracle.csr_spmv(probe, x, nthreads=nth, guided=guided)
+        per_row = (time.perf_counter() - t0) / 3 / probe.nrows
+        nrow = int(max(1, min(W["nrows"], budget / max(calls * per_row, 1e-12))))
+        S = W["host"](nrow)
+        total_nnz = W["nnz"]
+    else:
+        A = W["host"]()
+        zeta = oracle.zeta(A.row_lengths().astype(np.int32))
+        guided = zeta >= 0.4
+        t0 = time.perf_counter()
+        oracle.csr_spmv(A, x, nthreads=nth, guided=guided)
+        t_full = time.perf_counter() - t0
+        frac = min(1.0, budget / max(calls * t_full, 1e-9))
+        nrow = max(1, int(A.nrows * frac))
+        S = synth.CSR(nrow, A.ncols, A.rpt[:nrow + 1].copy(), A.col[:A.rpt[nrow]], A.val[:A.rpt[nrow]])
+        total_nnz = A.nnz
     for _ in range(args.warmup):
         oracle.csr_spmv(S, x, nthreads=nth, guided=guided)
     t0 = time.perf_counter()
@@ -339,13 +452,13 @@ def run_reference(args):
         oracle.csr_spmv(S, x, nthreads=nth, guided=guided)
     dt = time.perf_counter() - t0
     gf = 2.0 * S.nnz * args.steps / dt / 1e9
-    sample = (f"rows 0..{nrow - 1} of the workload ({S.nnz} nnz, {100 * frac:.2f}% of it) per step, "
-              f"binary64 CRS SpMV, OpenMP {'GUIDED,1' if guided else 'STATIC'}")
+    sample = (f"rows 0..{nrow - 1} of the workload ({S.nnz} nnz, {100 * S.nnz / total_nnz:.2f}% of it) per step, "
+              f"binary64 CRS SpMV, OpenMP {'GUIDED,1' if guided else 'STATIC'} on {nth} threads")
     line = {"impl": "reference", "metric": METRIC, "value": round(gf, 3), "unit": "GF/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(dt / args.steps * 1e3, 4), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc, "sample": sample},
+            "config": {"workload": W["desc"], "sample": sample},
             "cpu_baseline": {"value": round(gf, 3), "unit": "GF/s", "cores": nth, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(gf, 3), "unit": "GF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -366,10 +479,97 @@ def tune_launch(sell, h, xd, yd, stream, flags=0, blocks=(128, 256), unrolls=(1,
                 sell.sell_set_launch(h, *c)
             except sell.SellError:
                 continue
-            best_t[c] = min(best_t[c], time_spmv(sell, h, xd, yd, stream, reps=50, flags=flags))
+            best_t[c] = min(best_t[c], time_spmv(sell, h, xd, yd, stream, reps=30, flags=flags))
     c, t = min(best_t.items(), key=lambda kv: kv[1])
     sell.sell_set_launch(h, *c)
     return c[0], c[1], c[2], t
+
+
+def mixed_section(sell, model, csr_d, C, sigma, xd, y64, t64, stream, peak, comps):
+    """The same matrix with binary32 and bfloat16 values (binary32 x, y and
+    accumulation), each accumulation mode with its own tuned launch; error
+    against the binary64 product of the GPU."""
+    import torch
+    out = {}
+    x32 = xd.float()
+    nnz = int(csr_d.rpt[-1])
+    for name, st in (("f32", sell.SELL_F32), ("bf16", sell.SELL_BF16)):
+        hm = sell.sell_build(csr_d, C=C, sigma=sigma, store_type=st, stream=stream)
+        inf = hm.info
+        y32 = torch.empty(inf.nrows, dtype=torch.float32, device="cuda")
+        vb = 4 if st == sell.SELL_F32 else 2
+        alg = model.algorithmic_bytes(inf.nrows, inf.ncols, nnz, inf.nchunks, C, vb, 4, inf.has_perm)
+        row = {}
+        for tag, fl in comps:
+            blk, unr, pip, _ = tune_launch(sell, hm, x32, y32, stream, flags=fl)
+            dt = time_spmv(sell, hm, x32, y32, stream, reps=100, flags=fl)
+            torch.cuda.synchronize()
+            err = (y32.double() - y64).abs()
+            row[tag] = {"gflops": round(2.0 * nnz / dt / 1e9, 1), "us": round(dt * 1e6, 2),
+                        "gbs": round(alg / dt / 1e9, 1), "hbm_frac": round(alg / dt / 1e9 / peak, 4),
+                        "speedup_vs_f64": round(t64 / dt, 3), "block": blk, "unroll": unr, "pipeline": pip,
+                        "max_abs_err_vs_f64": float(err.max()), "rel_err_vs_f64": float(err.norm() / y64.norm())}
+        out[name] = row
+        hm.free()
+    return out
+
+
+def lognormal_section(sell, autotune, model, stream, peak, gather_gps, fma_tf):
+    """The lognormal random matrix, N = 2,000,000 (irregular, random columns):
+    the C x sigma sweep of the paper's Sec. 5.3 with the autotuner's choice,
+    its HBM and L2-gather bounds, cold calls, SpMMV and reduced precision."""
+    import torch
+    from paper_1307_6209_gb300 import synth
+    n = 2_000_000
+    A = synth.lognormal(n, mean=16.0, sigma_ln=1.2, cap=2000, seed=0)
+    csr_d = to_device(A)
+    x = torch.from_numpy(synth.vector(n, seed=0)).cuda()
+    y = torch.empty(n, dtype=torch.float64, device="cuda")
+    tr = autotune.tune(csr_d, store_type=sell.SELL_F64, Cs=(32, 64, 128), sigmas=(1, 256, 4096, n),
+                       blocks=(128, 256, 512), unrolls=(1, 2, 4, 8), pipelines=(0, 1, 2), keep=2, stream=stream,
+                       use_cache=False, cache=None)
+    best = tr.best
+    h = autotune.build_tuned(csr_d, best, stream=stream)
+    inf = h.info
+    dt = time_spmv(sell, h, x, y, stream, reps=500)
+    alg = model.algorithmic_bytes(n, n, A.nnz, inf.nchunks, best.C, 8, 8, inf.has_perm)
+    out = {"workload": f"lognormal random N={n} (row length mean 16, log-sd 1.2, cap 2000), nnz={A.nnz}, FP64",
+           "nnz": A.nnz, "tuned": {"C": best.C, "sigma": best.sigma, "block": best.block, "unroll": best.unroll,
+                                   "pipeline": best.pipeline},
+           "beta": round(inf.beta, 6), "zeta": round(inf.zeta, 3),
+           "us": round(dt * 1e6, 2), "gflops": round(2.0 * A.nnz / dt / 1e9, 1),
+           "gbs": round(alg / dt / 1e9, 1), "hbm_frac": round(alg / dt / 1e9 / peak, 4),
+           "kernel": kernel_name(best, best.C, inf),
+           "gather_bound": {"achieved_ggps": round(A.nnz / dt / 1e9, 1), "peak_ggps_measured": round(gather_gps, 1),
+                            "frac": round(A.nnz / dt / 1e9 / gather_gps, 4),
+                            "bound_us": round(A.nnz / gather_gps / 1e3, 2)},
+           "fp64_pipe_frac": round(2.0 * A.nnz / dt / 1e12 / fma_tf, 4),
+           "sweep": [{"C": f["C"], "sigma": f["sigma"], "beta": round(f["beta"], 4), "us": round(f["us"], 2),
+                      "gflops": round(2.0 * A.nnz / f["us"] / 1e3, 1), "build_ms": round(f["build_ms"], 2)}
+                     for f in sorted(tr.formats, key=lambda f: (f["C"], f["sigma"]))]}
+    nnzr = A.nnz / n
+    bal = model.balance_sell(1.0 / nnzr, inf.beta, nnzr)
+    out["paper_model"] = {"balance_bytes_per_flop": round(bal, 4),
+                          "model_bytes_per_launch": int(model.paper_model_bytes(A.nnz, inf.beta, n, n))}
+    cold = time_spmv_cold(sell, h, x, y, stream)
+    out["cold_us"] = round(cold * 1e6, 2)
+    spmmv = {}
+    for k in (4, 8):
+        Xd = x[:, None].repeat(1, k).contiguous()
+        Yd = torch.empty((n, k), dtype=torch.float64, device="cuda")
+        t = time_spmmv(sell, h, Xd, Yd, stream, reps=50)
+        spmmv[f"k{k}"] = {"gflops": round(2.0 * A.nnz * k / t / 1e9, 1), "us": round(t * 1e6, 2)}
+        del Xd, Yd
+    out["spmmv_f64"] = spmmv
+    sell.sell_spmv(h, x, y, stream=stream)
+    torch.cuda.synchronize()
+    out["mixed"] = mixed_section(sell, model, csr_d, best.C, best.sigma, x, y.clone(), dt, stream, peak,
+                                 (("plain", 0), ("dot2", sell.SELL_SPMV_COMPENSATED),
+                                  ("dot2_long_rows", sell.SELL_SPMV_COMPENSATED_LONG)))
+    h.free()
+    del csr_d, A
+    torch.cuda.empty_cache()
+    return out
 
 
 def laplace_section(sell, stream, reps=2000):
@@ -405,48 +605,6 @@ def laplace_section(sell, stream, reps=2000):
             "us_per_call_in_graph": round(graph * 1e6, 2), "gflops": round(2.0 * A.nnz / eager / 1e9, 2)}
 
 
-def stencil_section(sell, model, stream, peak, fma_tf, n=200):
-    """27-point stencil on n^3 (generated on the device): binary64, binary32 and
-    bfloat16 storage, each with its tuned launch."""
-    import torch
-    from paper_1307_6209_gb300 import synth
-    A = synth.stencil27_device(n, perturb=0.1, seed=0)
-    x = torch.rand(A.ncols, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(0)) * 2 - 1
-    out = {"workload": f"27-point stencil {n}^3, N={A.nrows}, nnz={A.nnz}, SELL-32-1", "nnz": A.nnz}
-    y64 = None
-    for name, st in (("f64", sell.SELL_F64), ("f32", sell.SELL_F32), ("bf16", sell.SELL_BF16)):
-        t0 = time.perf_counter()
-        h = sell.sell_build(A, C=32, sigma=1, store_type=st, stream=stream)
-        bms = (time.perf_counter() - t0) * 1e3
-        xs = x if st == sell.SELL_F64 else x.float()
-        ys = torch.empty(A.nrows, dtype=xs.dtype, device="cuda")
-        blk, unr, pip, _ = tune_launch(sell, h, xs, ys, stream)
-        dt = time_spmv(sell, h, xs, ys, stream, reps=200)
-        torch.cuda.synchronize()
-        vb = 8 if st == sell.SELL_F64 else (4 if st == sell.SELL_F32 else 2)
-        xb = 8 if st == sell.SELL_F64 else 4
-        alg = model.algorithmic_bytes(A.nrows, A.ncols, A.nnz, h.info.nchunks, 32, vb, xb, False)
-        row = {"us": round(dt * 1e6, 2), "gflops": round(2.0 * A.nnz / dt / 1e9, 1),
-               "gbs": round(alg / dt / 1e9, 1), "hbm_frac": round(alg / dt / 1e9 / peak, 4),
-               "block": blk, "unroll": unr, "pipeline": pip, "build_ms": round(bms, 1),
-               "beta": round(h.info.beta, 6)}
-        if st == sell.SELL_F64:
-            y64 = ys.clone()
-            if fma_tf:
-                row["fp64_pipe_frac"] = round(2.0 * A.nnz / dt / 1e12 / fma_tf, 4)
-            t64 = dt
-        else:
-            err = (ys.double() - y64).abs()
-            row["speedup_vs_f64"] = round(t64 / dt, 3)
-            row["max_abs_err_vs_f64"] = float(err.max())
-            row["rel_err_vs_f64"] = float(err.norm() / y64.norm())
-        out[name] = row
-        h.free()
-    del A
-    torch.cuda.empty_cache()
-    return out
-
-
 def _time_graph(g, stream, reps):
     """Average time of one replay; the replays run on `stream`, where the
     events are recorded (a graph replays on the current stream)."""
@@ -463,20 +621,20 @@ def _time_graph(g, stream, reps):
     return a.elapsed_time(b) * 1e-3 / reps
 
 
-def batched_section(sell, autotune, stream, nmat=512, ks=(1, 4, 8), seed=0):
+def batched_section(sell, autotune, model, stream, peak, gather_gps, nmat=512, ks=(1, 4, 8), seed=0):
     """512 matrices, rows U[1k, 200k], half banded (bandwidth 64, 7-30 per
     row), half lognormal; FP32 storage; k right-hand sides; C and sigma tuned
-    per class.  One persistent launch (CUDA graph) against per-matrix launches
-    and against the same batch in FP64."""
+    per class.  One plan per k (CUDA graph) against per-matrix launches and
+    against the same batch in FP64.  Every product of the plan is checked
+    bitwise against the same product alone."""
     import torch
     from paper_1307_6209_gb300 import synth
     gen = {"banded": synth.banded_device, "lognormal": synth.lognormal_device}
-    rng = np.random.default_rng(seed)
-    sizes = rng.integers(1000, 200001, nmat)
-    # C and sigma per class, tuned for batch throughput: every candidate runs a
-    # batch of 16 sample matrices of the class (a single small matrix is
-    # latency-bound and would favour formats that move more bytes)
+    recipe = synth.batch_set(nmat, seed=seed)
+    rng = np.random.default_rng(seed + 1)
     # C and sigma per class, tuned for batch throughput on 16 sample matrices
+    # (a single small matrix is latency-bound and would favour formats that
+    # move more bytes)
     choice = {}
     for cls in ("banded", "lognormal"):
         samples = [gen[cls](int(n), seed=900 + j) for j, n in enumerate(rng.integers(1000, 200001, 16))]
@@ -484,25 +642,25 @@ def batched_section(sell, autotune, stream, nmat=512, ks=(1, 4, 8), seed=0):
         choice[cls] = {"C": best["C"], "sigma": best["sigma"],
                        "candidates": [{k: (round(v, 1) if k == "us" else v) for k, v in t.items()} for t in table]}
         del samples
-    h32, h64, nnz = [], [], 0
+    h32, h64, kinds, nnz = [], [], [], 0
     t0 = time.perf_counter()
-    for i, n in enumerate(sizes):
-        cls = "banded" if i % 2 == 0 else "lognormal"
-        A = gen[cls](int(n), seed=i)
-        ch = choice[cls]
+    for kind, n, s in recipe:
+        A = gen[kind](n, seed=s)
+        ch = choice[kind]
         h32.append(sell.sell_build(A, C=ch["C"], sigma=ch["sigma"], store_type=sell.SELL_F32, stream=stream))
         h64.append(sell.sell_build(A, C=ch["C"], sigma=ch["sigma"], store_type=sell.SELL_F64, stream=stream))
+        kinds.append(kind)
         nnz += A.nnz
         del A
     build_s = time.perf_counter() - t0
     out = {"workload": f"{nmat} matrices, rows U[1000, 200000], half banded (bw 64, 7-30/row), half lognormal",
-           "nnz_total": nnz, "rows_total": int(sizes.sum()),
+           "nnz_total": nnz, "rows_total": int(sum(n for _, n, _ in recipe)),
            "tuned": {c: {"C": v["C"], "sigma": v["sigma"]} for c, v in choice.items()},
            "tuning_candidates": {c: v["candidates"] for c, v in choice.items()},
            "build_s_both_precisions": round(build_s, 2)}
     for k in ks:
         row = {}
-        for tag, hs, dt in (("f32", h32, torch.float32), ("f64", h64, torch.float64)):
+        for tag, hs, dt, vb in (("f32", h32, torch.float32, 4), ("f64", h64, torch.float64, 8)):
             items = []
             for h in hs:
                 shp_x = (h.info.ncols,) if k == 1 else (h.info.ncols, k)
@@ -516,6 +674,7 @@ def batched_section(sell, autotune, stream, nmat=512, ks=(1, 4, 8), seed=0):
             with torch.cuda.graph(g, stream=stream):
                 plan.run(stream=stream)
             t_batch = _time_graph(g, stream, 20)
+            batch_y = [Y.clone() for _, _, Y, _ in items]
 
             def per_matrix():
                 for h, X, Y, _ in items:
@@ -525,6 +684,8 @@ def batched_section(sell, autotune, stream, nmat=512, ks=(1, 4, 8), seed=0):
                         sell.sell_spmmv(h, X, Y, stream=stream)
             per_matrix()
             torch.cuda.synchronize()
+            same = all(torch.equal(a, Y) for a, (_, _, Y, _) in zip(batch_y, items))
+            del batch_y
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             for _ in range(3):
@@ -536,11 +697,25 @@ def batched_section(sell, autotune, stream, nmat=512, ks=(1, 4, 8), seed=0):
             with torch.cuda.graph(g2, stream=stream):
                 per_matrix()
             t_pm_graph = _time_graph(g2, stream, 5)
+            # bound weighted by class: the banded products at the HBM copy
+            # bandwidth, the lognormal ones (random columns) at the measured
+            # L2 gather rate (or HBM, whichever is slower)
+            alg = {"banded": 0, "lognormal": 0}
+            gath = 0
+            for h, kind in zip(hs, kinds):
+                inf = h.info
+                alg[kind] += model.algorithmic_bytes(inf.nrows, inf.ncols, inf.nnz, inf.nchunks, inf.C, vb, vb,
+                                                     inf.has_perm, k=k)
+                gath += inf.nnz if kind == "lognormal" else 0
+            t_bound = alg["banded"] / (peak * 1e9) + max(alg["lognormal"] / (peak * 1e9), gath / (gather_gps * 1e9))
             row[tag] = {"batch_ms": round(t_batch * 1e3, 3), "gflops": round(2.0 * nnz * k / t_batch / 1e9, 1),
+                        "hbm_frac": round((alg["banded"] + alg["lognormal"]) / t_batch / 1e9 / peak, 4),
+                        "class_bound_ms": round(t_bound * 1e3, 3), "class_bound_frac": round(t_bound / t_batch, 4),
                         "per_matrix_eager_ms": round(t_eager * 1e3, 3),
                         "per_matrix_graph_ms": round(t_pm_graph * 1e3, 3),
                         "speedup_vs_per_matrix_eager": round(t_eager / t_batch, 2),
-                        "speedup_vs_per_matrix_graph": round(t_pm_graph / t_batch, 2)}
+                        "speedup_vs_per_matrix_graph": round(t_pm_graph / t_batch, 2),
+                        "batch_equals_per_matrix": same}
             plan.free()
             del g, g2, items
         row["f32_speedup_vs_f64"] = round(row["f64"]["batch_ms"] / row["f32"]["batch_ms"], 3)
@@ -646,12 +821,59 @@ def pathological_section(sell, model, stream, peak):
     return out
 
 
+def compact_summary(line, ex):
+    """Every figure of the line in a few hundred bytes (placed last, so a
+    truncated tail of the output still shows it)."""
+    def g(d, *path):
+        for p in path:
+            if not isinstance(d, dict) or p not in d:
+                return None
+            d = d[p]
+        return d
+
+    s = {"headline": {"gf": line["value"], "hbm": line["roofline"]["frac"], "us": line["roofline"]["kernel_avg_us"],
+                      "e2e_gf": g(line, "e2e", "value")}}
+    for tag in ("f32", "bf16"):
+        r = g(ex, "mixed", tag, "plain")
+        if r:
+            s[f"headline_{tag}"] = {"gf": r["gflops"], "hbm": r["hbm_frac"], "x_f64": r["speedup_vs_f64"],
+                                    "rel_err": float(f"{r['rel_err_vs_f64']:.2e}")}
+    ln = ex.get("lognormal2M")
+    if isinstance(ln, dict) and "gflops" in ln:
+        s["lognormal2M"] = {"gf": ln["gflops"], "hbm": ln["hbm_frac"], "gather": ln["gather_bound"]["frac"],
+                            "C": ln["tuned"]["C"], "sigma": ln["tuned"]["sigma"]}
+        for tag in ("f32", "bf16"):
+            r = g(ln, "mixed", tag, "plain")
+            if r:
+                s[f"lognormal2M_{tag}"] = {"gf": r["gflops"], "x_f64": r["speedup_vs_f64"],
+                                           "rel_err": float(f"{r['rel_err_vs_f64']:.2e}")}
+    b = ex.get("batched")
+    if isinstance(b, dict) and "k1" in b:
+        s["batch512_f32"] = {f"k{k}": {"gf": g(b, f"k{k}", "f32", "gflops"), "hbm": g(b, f"k{k}", "f32", "hbm_frac"),
+                                       "bound": g(b, f"k{k}", "f32", "class_bound_frac"),
+                                       "x_f64": g(b, f"k{k}", "f32_speedup_vs_f64"),
+                                       "ok": g(b, f"k{k}", "f32", "batch_equals_per_matrix")} for k in (1, 4, 8)}
+    v = ex.get("serving")
+    if isinstance(v, dict) and "load_0.5" in v:
+        s["serving"] = {"sat_rps": v["saturated_req_per_s"]}
+        for f in ("0.5", "0.8", "0.95"):
+            s["serving"][f"p50_p99_ms_{f}"] = [round(g(v, f"load_{f}", "p50_ms"), 2),
+                                               round(g(v, f"load_{f}", "p99_ms"), 2)]
+    lp = ex.get("laplace64")
+    if isinstance(lp, dict) and "us_per_call" in lp:
+        s["laplace64_us"] = [lp["us_per_call"], lp["us_per_call_in_graph"]]
+    errs = [k for k, v in ex.items() if isinstance(v, dict) and "error" in v]
+    if errs:
+        s["section_errors"] = errs
+    return s
+
+
 def run_ours(args):
     import torch
     from paper_1307_6209_gb300 import autotune
     from paper_1307_6209_gb300 import build as cuda_build
     from paper_1307_6209_gb300 import dist as sdist
-    from paper_1307_6209_gb300 import model, sell
+    from paper_1307_6209_gb300 import model, sell, synth
 
     ws, rank, local = dist_setup()
     torch.cuda.set_device(local)
@@ -662,28 +884,38 @@ def run_ours(args):
     cuda_build.build()
     sell.load()
     stream = torch.cuda.Stream()
-    A, x, desc, grid = make_workload(args)
+    W = workload(args)
     n_gpus = ws
     dev_name = torch.cuda.get_device_name(local)
     peak, peak_src = load_peaks()
+    smi = SmiClocks(local).start()
+    nvml = NvmlClocks(local).start()
+    extras = {}
 
     with torch.cuda.stream(stream):
+        t_sec = time.perf_counter()
+        A_host = None
+        if W["device"] is not None:
+            csr_d = W["device"]()
+        else:
+            A_host = W["host"]()
+            csr_d = to_device(A_host)
+        nrows, ncols, nnz = int(csr_d.nrows), int(csr_d.ncols), int(csr_d.rpt[-1])
+        x = synth.vector(ncols, seed=0)
         xd = torch.from_numpy(x).cuda()
-        yd = torch.empty(A.nrows, dtype=torch.float64, device="cuda")
-        csr_d = type(A)(A.nrows, A.ncols, torch.from_numpy(A.rpt).cuda(), torch.from_numpy(A.col).cuda(),
-                        torch.from_numpy(A.val).cuda())
+        yd = torch.empty(nrows, dtype=torch.float64, device="cuda")
         torch.cuda.synchronize()
 
         # ---- measuring kernels: read bandwidth b, random-gather rate, FP64 FMA peak
         b_read = measure_read_bw(sell, stream)
-        gather_gps = measure_gather(sell, stream, max(A.ncols, 1))
+        gather_gps = measure_gather(sell, stream, 2_000_000)
         fma_tf = measure_fp64_fma(sell, stream)
 
-        # ---- autotuner: stage 1 = the (C, sigma) sweep, stage 2 = launch shapes
+        # ---- autotuner: stage 1 = the (C, sigma) candidates, stage 2 = launch shapes
         if args.C is not None or args.sigma is not None or args.no_sweep:
             Cs, sigmas = (args.C or 32,), (args.sigma or 1,)
         else:
-            Cs, sigmas = sorted({c for c, _ in grid}), sorted({s for _, s in grid})
+            Cs, sigmas = sorted({c for c, _ in W["grid"]}), sorted({s for _, s in W["grid"]})
         blocks = (args.block,) if args.block else (128, 256, 512)
         unrolls = (args.unroll,) if args.unroll else (1, 2, 4, 8)
         pipelines = (args.pipeline,) if args.pipeline is not None else (0, 1, 2)
@@ -697,12 +929,11 @@ def run_ours(args):
         build_ms = (time.perf_counter() - t0) * 1e3
         inf = h.info
         sweep = [{"C": f["C"], "sigma": f["sigma"], "beta": round(f["beta"], 4), "us": round(f["us"], 2),
-                  "gflops": round(2.0 * A.nnz / f["us"] / 1e3, 1), "build_ms": round(f["build_ms"], 2)}
+                  "gflops": round(2.0 * nnz / f["us"] / 1e3, 1), "build_ms": round(f["build_ms"], 2)}
                  for f in sorted(tr.formats, key=lambda f: (f["C"], f["sigma"]))]
+        smi.section("setup_and_tuning", t_sec, time.perf_counter())
 
         # ---- the timed region: K steps of one SpMV each
-        clk = ClockSampler(local)
-        clk.start()
         for _ in range(args.warmup):
             sell.sell_spmv(h, xd, yd, stream=stream)
         ev_a = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -711,7 +942,7 @@ def run_ours(args):
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-        wall0 = time.time()
+        pc0 = time.perf_counter()
         torch.cuda.nvtx.range_push("timed_region")
         t_start.record(stream)
         for i in range(args.steps):
@@ -721,28 +952,45 @@ def run_ours(args):
         t_end.record(stream)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
+        pc1 = time.perf_counter()
         if dist:
             dist.barrier()
-        wall1 = time.time()
-        clk.stop()
+        smi.section("timed_region", pc0, pc1)
         total_s = t_start.elapsed_time(t_end) * 1e-3
         kern_s = sum(a.elapsed_time(b) for a, b in zip(ev_a, ev_b)) * 1e-3 / args.steps
-        flops = 2.0 * A.nnz
+        flops = 2.0 * nnz
         # weak scaling: every rank's flops over the slowest rank's time
         value = sdist.weak_scaling_throughput(flops * args.steps, total_s, device="cuda") / 1e9
         step_s = sdist.max_over_ranks(total_s, device="cuda") / args.steps
+        clocks = nvml.summary(pc0, pc1) or smi.summary(pc0, pc1)
 
-        extras = {}
+        # ---- the same product back to back for about a second: the clock
+        # under sustained load next to the rate it gives
+        reps = max(1, int(1.0 / max(kern_s, 1e-6)))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        pcs0 = time.perf_counter()
+        a.record(stream)
+        for _ in range(reps):
+            sell.sell_spmv(h, xd, yd, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        pcs1 = time.perf_counter()
+        smi.section("sustained", pcs0, pcs1)
+        sus_s = a.elapsed_time(b) * 1e-3 / reps
+        extras["sustained"] = {"calls": reps, "gflops": round(flops / sus_s / 1e9, 2), "us": round(sus_s * 1e6, 2),
+                               "clocks": nvml.summary(pcs0, pcs1) or smi.summary(pcs0, pcs1)}
+
         e2e = None
         if not args.no_extras:
             # ---- end to end through the C ABI with host buffers (pinned): each
             # step copies its x in and its y out; steps alternate two streams
             # (and two pinned buffer pairs), so one step's copies overlap the
             # previous step's kernel -- the library orders the kernels
+            t_sec = time.perf_counter()
             xh = [torch.from_numpy(x).pin_memory() for _ in range(2)]
-            yh = [torch.empty(A.nrows, dtype=torch.float64).pin_memory() for _ in range(2)]
+            yh = [torch.empty(nrows, dtype=torch.float64).pin_memory() for _ in range(2)]
             io_streams = [stream, torch.cuda.Stream()]
-            ke = min(args.steps, 2000)
+            ke = min(max(args.steps, 20), 2000)
             for i in range(6):
                 sell.sell_spmv(h, xh[i % 2], yh[i % 2], flags=sell.SELL_SPMV_HOST_IO, stream=io_streams[i % 2])
             torch.cuda.synchronize()
@@ -758,89 +1006,81 @@ def run_ours(args):
             e2e_check = bool(np.array_equal(yh[0].numpy(), yh[1].numpy())) and \
                 yh[0].numpy().tobytes() == yd.cpu().numpy().tobytes()
             e2e = {"value": round(n_gpus * flops / e2e_s / 1e9, 2), "unit": "GF/s",
-                   "h2d_bytes_per_step": 8 * A.ncols, "d2h_bytes_per_step": 8 * A.nrows,
-                   "streams": 2, "result_equals_device_run": e2e_check}
+                   "h2d_bytes_per_step": 8 * ncols, "d2h_bytes_per_step": 8 * nrows,
+                   "steps": ke, "streams": 2, "result_equals_device_run": e2e_check}
+            del xh, yh
+            smi.section("e2e", t_sec, time.perf_counter())
 
             # ---- multiple right-hand sides (A streamed once for k vectors)
+            t_sec = time.perf_counter()
             spmmv = {}
             for k in (4, 8):
-                Xd = torch.from_numpy(np.tile(x[:, None], (1, k))).cuda()
-                Yd = torch.empty((A.nrows, k), dtype=torch.float64, device="cuda")
-                dt = time_spmmv(sell, h, Xd, Yd, stream, reps=50)
-                spmmv[f"k{k}"] = {"gflops": round(2.0 * A.nnz * k / dt / 1e9, 1), "us": round(dt * 1e6, 2)}
+                Xd = xd[:, None].repeat(1, k).contiguous()
+                Yd = torch.empty((nrows, k), dtype=torch.float64, device="cuda")
+                dt = time_spmmv(sell, h, Xd, Yd, stream, reps=20)
+                spmmv[f"k{k}"] = {"gflops": round(2.0 * nnz * k / dt / 1e9, 1), "us": round(dt * 1e6, 2)}
                 del Xd, Yd
             extras["spmmv_f64"] = spmmv
 
-            # ---- cold: L2 flushed before each call (x must come from HBM again)
+            # ---- cold: L2 flushed before each call
             cold_s = time_spmv_cold(sell, h, xd, yd, stream)
             extras["cold"] = {"us": round(cold_s * 1e6, 2), "gflops": round(flops / cold_s / 1e9, 1),
-                              "warm_us": round(kern_s * 1e6, 2),
-                              "note": "256 MB written between calls; warm = the timed region (x L2-resident)"}
+                              "warm_us": round(kern_s * 1e6, 2), "note": "256 MB written between calls"}
 
-            # ---- reduced-precision storage: binary32 / bfloat16 values, binary32 accumulation
-            mixed = {}
+            # ---- FP64 vs mixed: binary32 / bfloat16 values, binary32 accumulation
             sell.sell_spmv(h, xd, yd, stream=stream)
-            y64 = yd.clone()
-            x32 = xd.float()
-            for name, st in (("f32", sell.SELL_F32), ("bf16", sell.SELL_BF16)):
-                hm = sell.sell_build(csr_d, C=C, sigma=sigma, store_type=st, stream=stream)
-                y32 = torch.empty(A.nrows, dtype=torch.float32, device="cuda")
-                row = {}
-                for tag, fl in (("plain", 0), ("dot2", sell.SELL_SPMV_COMPENSATED),
-                                ("dot2_long_rows", sell.SELL_SPMV_COMPENSATED_LONG)):
-                    blk, unr, pip, _ = tune_launch(sell, hm, x32, y32, stream, flags=fl)
-                    dt = time_spmv(sell, hm, x32, y32, stream, reps=100, flags=fl)
-                    torch.cuda.synchronize()
-                    err = (y32.double() - y64).abs()
-                    row[tag] = {"gflops": round(flops / dt / 1e9, 1), "us": round(dt * 1e6, 2),
-                                "speedup_vs_f64": round(kern_s / dt, 3), "block": blk, "unroll": unr,
-                                "pipeline": pip,
-                                "max_abs_err_vs_f64": float(err.max()),
-                                "rel_err_vs_f64": float(err.norm() / y64.norm())}
-                mixed[name] = row
-                hm.free()
-            extras["mixed"] = mixed
+            torch.cuda.synchronize()
+            comps = [("plain", 0), ("dot2", sell.SELL_SPMV_COMPENSATED)]
+            if inf.max_row_len > 64:
+                comps.append(("dot2_long_rows", sell.SELL_SPMV_COMPENSATED_LONG))
+            extras["mixed"] = mixed_section(sell, model, csr_d, C, sigma, xd, yd.clone(), kern_s, stream, peak,
+                                            comps)
+            smi.section("spmmv_cold_mixed", t_sec, time.perf_counter())
+        if A_host is None and rank == 0 and ws == 1 and not args.no_cpu:
+            A_host = to_host(csr_d)  # the matrix the GPU multiplied, for the CPU baseline
         del csr_d
+        h.free()
         torch.cuda.empty_cache()
-        if not args.no_extras and args.workload == "lognormal" and rank == 0:
+        if not args.no_extras and rank == 0:
             # each extra section reports its own failure instead of losing the line
-            for key, fn in (("laplace64", lambda: laplace_section(sell, stream)),
-                            ("stencil27", lambda: stencil_section(sell, model, stream, peak, fma_tf)),
-                            ("pathological", lambda: pathological_section(sell, model, stream, peak)),
-                            ("batched", lambda: batched_section(sell, autotune, stream)),
-                            ("serving", lambda: serving_section(sell, stream))):
+            sections = [("lognormal2M", lambda: lognormal_section(sell, autotune, model, stream, peak, gather_gps,
+                                                                  fma_tf)),
+                        ("laplace64", lambda: laplace_section(sell, stream)),
+                        ("pathological", lambda: pathological_section(sell, model, stream, peak)),
+                        ("batched", lambda: batched_section(sell, autotune, model, stream, peak, gather_gps)),
+                        ("serving", lambda: serving_section(sell, stream))]
+            if W["name"] == "lognormal":
+                sections = sections[1:]
+            for key, fn in sections:
+                t_sec = time.perf_counter()
                 try:
                     extras[key] = fn()
                 except Exception as e:  # noqa: BLE001 -- recorded in the JSON line
                     extras[key] = {"error": f"{type(e).__name__}: {e}"}
                     torch.cuda.synchronize()
                     torch.cuda.empty_cache()
+                smi.section(key, t_sec, time.perf_counter())
 
     # ---- roofline of the dominant kernel (the SpMV)
-    alg = model.algorithmic_bytes(A.nrows, A.ncols, A.nnz, inf.nchunks, C, 8, 8, inf.has_perm)
+    alg = model.algorithmic_bytes(nrows, ncols, nnz, inf.nchunks, C, 8, 8, inf.has_perm)
     achieved = alg / kern_s / 1e9
-    wl_key = f"{args.workload}:N{A.nrows}"
+    wl_key = f"{W['name']}:N{nrows}"
     traffic, _ = lookup_traffic(wl_key)
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": traffic,
             "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
             "kernel": kernel_name(best, C, inf),
             "kernel_avg_us": round(kern_s * 1e6, 3), "algorithmic_bytes_per_launch": alg}
-    nnzr = A.nnz / A.nrows
+    nnzr = nnz / nrows
     bal = model.balance_sell(1.0 / nnzr, inf.beta, nnzr)
-    extras["gather_bound"] = {
-        "note": "every nonzero gathers one x element from L2 (x is L2-resident): random columns are bound "
-                "by the L2 scattered-sector rate measured by sell_bench_gather",
-        "gathers_per_launch": A.nnz, "achieved_ggps": round(A.nnz / kern_s / 1e9, 1),
-        "peak_ggps_measured": round(gather_gps, 1), "frac": round(A.nnz / kern_s / 1e9 / gather_gps, 4),
-        "bound_us": round(A.nnz / gather_gps / 1e3, 2)}
     extras["paper_model"] = {
         "beta": inf.beta, "nnzr": round(nnzr, 3), "zeta": round(inf.zeta, 3),
         "balance_bytes_per_flop": round(bal, 4),
         "bound_gflops_b_read": round(model.roofline(b_read, bal), 1),
         "frac_of_model_bound": round(value / n_gpus / model.roofline(b_read, bal), 4),
-        "model_bytes_per_launch": int(model.paper_model_bytes(A.nnz, inf.beta, A.nrows, A.ncols))}
+        "model_bytes_per_launch": int(model.paper_model_bytes(nnz, inf.beta, nrows, ncols))}
     extras["b_read_gbs"] = round(b_read, 1)
+    extras["gather_peak_ggps"] = round(gather_gps, 1)
     extras["fp64_fma_peak_tflops"] = round(fma_tf, 3)
     extras["fp64_pipe_frac"] = round(flops / kern_s / 1e12 / fma_tf, 4)
     extras["build_ms"] = round(build_ms, 2)
@@ -849,24 +1089,30 @@ def run_ours(args):
     extras["sweep"] = sweep
     extras["device"] = dev_name
 
+    cb = None
+    if rank == 0 and not args.no_cpu and ws == 1:
+        t_sec = time.perf_counter()
+        cb = cpu_baseline(A_host, x, W["name"])
+        smi.section("cpu_baseline", t_sec, time.perf_counter())
+    nvml.stop()
+    smi.stop()
+    extras["clocks_by_section"] = smi.by_section()
     if rank == 0:
-        cb = None
-        if not args.no_cpu and ws == 1:
-            cb = cpu_baseline(A, x)
         line = {
             "metric": METRIC, "value": round(value, 2), "unit": "GF/s",
             "n_gpus": n_gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(step_s * 1e3, 5), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc, "C": C, "sigma": sigma, "nrows": A.nrows, "nnz": A.nnz,
+            "config": {"workload": W["desc"], "C": C, "sigma": sigma, "nrows": nrows, "nnz": nnz,
                        "beta": round(inf.beta, 6), "stored": inf.stored,
                        "l2": f"inputs larger than L2: the matrix streams {alg / 1e9:.2f} GB per step "
-                             f"(L2 {L2_BYTES / 2 ** 20:.0f} MiB); x stays L2-resident by design",
+                             f"(L2 {L2_BYTES / 2 ** 20:.0f} MiB), no flush needed",
                        "parallelism": f"replicas x{n_gpus}"},
             "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": args.steps,
-            "clocks": clk.summary(wall0, wall1),
+            "clocks": clocks,
         }
         line.update(extras)
+        line["summary"] = compact_summary(line, extras)
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

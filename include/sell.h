@@ -260,6 +260,17 @@ SELL_API sell_status sell_set_launch(sell_handle h, int32_t block, int32_t unrol
  * SELL_ECUDA, SELL_ETIMEOUT. */
 SELL_API sell_status sell_check(sell_handle h, void *stream);
 
+/* Test hook of the failure route above (not in the paper): the next
+ * single-vector product of h that runs on the bulk-staged kernel (launch mode
+ * 2) makes its first warp wait, before its first piece, on a barrier that
+ * nothing ever completes, for limit_us microseconds (1..1000000).  That wait
+ * gives up; the warp drains its own copies in flight with the normal limit,
+ * records the failure and ends, so the product is incomplete and sell_check
+ * returns SELL_ETIMEOUT.  One launch only; later products are unaffected.
+ * No GPU fault is involved.  Errors: SELL_EINVAL, SELL_EUNSUPPORTED (the
+ * handle is not in launch mode 2). */
+SELL_API sell_status sell_test_expire_wait(sell_handle h, uint32_t limit_us);
+
 /* Fill *info (host struct).  Errors: SELL_EINVAL. */
 SELL_API sell_status sell_info(sell_handle h, sell_info_t *info);
 

@@ -203,9 +203,11 @@ sell_status sell_spmmv(sell_handle h, const void *X, int64_t ldx, void *Y, int64
     // device-to-host copy (event wait on this stream), and the products of
     // host-io calls run one after another whatever their streams (they share
     // the long-row scratch), so calls may alternate streams to overlap their
-    // copies with the previous call's kernels.
+    // copies with the previous call's kernels.  The slots hold X and Y
+    // densely (leading dimension k); only the k used columns of each host row
+    // are copied, so host columns k..ld-1 are neither read nor written.
     const size_t xs = h->store_type == SELL_F64 ? 8 : 4;
-    const size_t xb = (size_t)h->ncols * ldx * xs, yb = (size_t)h->nrows * ldy * xs;
+    const size_t xb = (size_t)h->ncols * k * xs, yb = (size_t)h->nrows * k * xs;
     sell_matrix::IoSlot &sl = h->io[h->io_next];
     if (!sl.done) SELL_CUDA_TRY(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
     if (!h->kdone) SELL_CUDA_TRY(cudaEventCreateWithFlags(&h->kdone, cudaEventDisableTiming));
@@ -213,13 +215,24 @@ sell_status sell_spmmv(sell_handle h, const void *X, int64_t ldx, void *Y, int64
     SELL_TRY(ensure_stage(h, &sl.x, &sl.xb, xb > 0 ? xb : 16, s));
     SELL_TRY(ensure_stage(h, &sl.y, &sl.yb, yb, s));
     h->io_next ^= 1;
-    if (xb) SELL_CUDA_TRY(cudaMemcpyAsync(sl.x, X, xb, cudaMemcpyHostToDevice, s));
-    if (flags & SELL_SPMV_ACCUMULATE) SELL_CUDA_TRY(cudaMemcpyAsync(sl.y, Y, yb, cudaMemcpyHostToDevice, s));
+    const size_t row = (size_t)k * xs;
+    if (xb) {
+        if (ldx == k) SELL_CUDA_TRY(cudaMemcpyAsync(sl.x, X, xb, cudaMemcpyHostToDevice, s));
+        else SELL_CUDA_TRY(cudaMemcpy2DAsync(sl.x, row, X, (size_t)ldx * xs, row, (size_t)h->ncols,
+                                             cudaMemcpyHostToDevice, s));
+    }
+    if (flags & SELL_SPMV_ACCUMULATE) {
+        if (ldy == k) SELL_CUDA_TRY(cudaMemcpyAsync(sl.y, Y, yb, cudaMemcpyHostToDevice, s));
+        else SELL_CUDA_TRY(cudaMemcpy2DAsync(sl.y, row, Y, (size_t)ldy * xs, row, (size_t)h->nrows,
+                                             cudaMemcpyHostToDevice, s));
+    }
     if (h->kdone_used) SELL_CUDA_TRY(cudaStreamWaitEvent(s, h->kdone, 0));
-    SELL_TRY(launch_spmmv(h, sl.x, ldx, sl.y, ldy, k, flags & ~SELL_SPMV_HOST_IO, s));
+    SELL_TRY(launch_spmmv(h, sl.x, k, sl.y, k, k, flags & ~SELL_SPMV_HOST_IO, s));
     SELL_CUDA_TRY(cudaEventRecord(h->kdone, s));
     h->kdone_used = true;
-    SELL_CUDA_TRY(cudaMemcpyAsync(Y, sl.y, yb, cudaMemcpyDeviceToHost, s));
+    if (ldy == k) SELL_CUDA_TRY(cudaMemcpyAsync(Y, sl.y, yb, cudaMemcpyDeviceToHost, s));
+    else SELL_CUDA_TRY(cudaMemcpy2DAsync(Y, (size_t)ldy * xs, sl.y, row, row, (size_t)h->nrows,
+                                         cudaMemcpyDeviceToHost, s));
     SELL_CUDA_TRY(cudaEventRecord(sl.done, s));
     sl.used = true;
     return SELL_OK;
@@ -279,6 +292,17 @@ sell_status sell_check(sell_handle h, void *stream) {
     if (v == 0) return SELL_OK;
     SELL_CUDA_TRY(cudaMemset(h->dstat, 0, sizeof(v)));
     return fail(SELL_ETIMEOUT, "sell_check: a bounded wait of the bulk-staged SpMV gave up");
+}
+
+sell_status sell_test_expire_wait(sell_handle h, uint32_t limit_us) {
+    if (!h) return fail(SELL_EINVAL, "sell_test_expire_wait: NULL handle");
+    if (limit_us == 0 || limit_us > 1000000u)
+        return fail(SELL_EINVAL, "sell_test_expire_wait: the limit must be 1..1000000 microseconds");
+    if (h->pipeline != 2 || h->bulk_grid <= 0)
+        return fail(SELL_EUNSUPPORTED, "sell_test_expire_wait: only the bulk-staged SpMV (launch mode 2) "
+                                       "waits on the device");
+    h->expire_us = limit_us;
+    return SELL_OK;
 }
 
 sell_status sell_info(sell_handle h, sell_info_t *info) {

@@ -100,6 +100,8 @@ struct sell_matrix {
     int64_t wsplit_n = 0;
     int32_t *dstat = nullptr;  // device status word: 1 after a bounded wait gave up
     int32_t bulk_grid = 0, bulk_warps = 0, bulk_ring = 0;
+    mutable uint32_t expire_us = 0;  // one-shot test hook of sell_test_expire_wait (0: off),
+                                     // consumed by the next bulk-staged launch
     double *dot_part = nullptr;  // range sums of sell_spmv_dot (lazily allocated)
     // host-io staging (lazily allocated): two slots used in turn, so that the
     // copies of one call overlap the kernel of the previous one when calls

@@ -25,7 +25,10 @@
 // for piece k, gather x for all its entries at once, and run the FMA chains
 // in entry order.  Every wait is bounded (kWaitNs); a wait that gives up sets
 // *dstat, waits (bounded) for the warp's copies still in flight and ends the
-// warp, and sell_check reports it.
+// warp, and sell_check reports it.  For testing that route, a launch may ask
+// (Args::expire_ns) that the first warp of the grid first waits, with that
+// short limit, on a barrier that nothing ever completes; the warp's real
+// copies are then drained with the normal limit before it ends.
 #pragma once
 
 #include "sell_rowdot.cuh"
@@ -46,10 +49,14 @@ struct Slot {  // byte offsets inside one slot (all 16-byte aligned)
     static constexpr int bytes = desc + 16;
 };
 
+// Byte size of the barrier region: R barriers per warp plus one that no copy
+// ever completes (the test barrier of Args::expire_ns).
+constexpr int bars_bytes(int W, int R) { return ((W * R + 1) * 8 + 15) / 16 * 16; }
+
 // Dynamic shared memory of a block of W warps with R slots each.
 template <class VT>
 constexpr size_t smem_bytes(int W, int R) {
-    return (size_t)((W * R * 8 + 15) / 16 * 16) + (size_t)W * R * Slot<VT>::bytes;
+    return (size_t)bars_bytes(W, R) + (size_t)W * R * Slot<VT>::bytes;
 }
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -91,14 +98,14 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// Wait for the phase of the given parity to complete; false after kWaitNs
+// Wait for the phase of the given parity to complete; false after limit_ns
 // (or 2^26 polls) without completion.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns = kWaitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (uint32_t i = 0; i < (1u << 26); ++i) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 255u) == 255u && global_ns() - t0 > kWaitNs) return false;
+        if ((i & 255u) == 255u && global_ns() - t0 > limit_ns) return false;
     }
     return false;
 }
@@ -133,6 +140,7 @@ struct Args {
     typename XType<VT>::T *Y;
     int64_t ldx, ldy, N, long_threads;
     int ring, accumulate;
+    uint64_t expire_ns;  // 0, or: warp 0 of block 0 first waits this long on the test barrier
 };
 
 // RPL = C / 32 rows per lane: lane l of a warp takes rows l, l + 32, ... of
@@ -147,13 +155,15 @@ __global__ void __launch_bounds__(512) k_spmv_bulk(const __grid_constant__ Args<
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
     const int R = a.ring;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem) + warp * R;
-    unsigned char *slots = smem + (W * R * 8 + 15) / 16 * 16 + (size_t)warp * R * S::bytes;
+    uint64_t *never = reinterpret_cast<uint64_t *>(smem) + W * R;  // no copy ever completes it
+    unsigned char *slots = smem + bars_bytes(W, R) + (size_t)warp * R * S::bytes;
     const int64_t wg = (int64_t)blockIdx.x * W + warp;
     const int64_t NW = (int64_t)gridDim.x * W;
     const uint64_t pol = l2_evict_first_policy();
 
     if (lane == 0) {
         for (int i = 0; i < R; ++i) mbar_init(bars + i, 1);
+        if (warp == 0) mbar_init(never, 1);
         fence_mbar_init();
     }
     __syncwarp();
@@ -240,7 +250,9 @@ __global__ void __launch_bounds__(512) k_spmv_bulk(const __grid_constant__ Args<
     for (int64_t k = 0; k < issued; ++k) {
         issue_next();  // piece k + R - 1 into the slot of piece k - 1
         const int slot = (int)(k % R);
-        const bool ok = mbar_wait(bars + slot, (uint32_t)((k / R) & 1));
+        bool ok = true;
+        if (a.expire_ns && k == 0 && wg == 0) ok = mbar_wait(never, 0, a.expire_ns);  // runs out
+        ok = ok && mbar_wait(bars + slot, (uint32_t)((k / R) & 1));
         if (__any_sync(0xffffffffu, !ok)) {
             if (lane == 0) atomicExch(a.dstat, 1);
             for (int64_t kk = k; kk < issued; ++kk) (void)mbar_wait(bars + kk % R, (uint32_t)((kk / R) & 1));
@@ -354,6 +366,8 @@ cudaError_t run(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64
     a.long_threads = h->nunits * h->C;
     a.ring = h->bulk_ring;
     a.accumulate = acc;
+    a.expire_ns = (uint64_t)h->expire_us * 1000u;
+    h->expire_us = 0;  // the test hook applies to one launch
     const size_t smem = smem_bytes<VT>(h->bulk_warps, h->bulk_ring);
     const void *fn = kernel_for_c<VT, Acc>(h->C, h->nunits > 0);
     cudaError_t e = allow_smem(fn, h->device);

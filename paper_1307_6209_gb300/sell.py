@@ -95,6 +95,7 @@ SIGNATURES = {
                                           ctypes.c_uint32, _P]),
     "sell_set_launch": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "sell_check": (ctypes.c_int, [_P, _P]),
+    "sell_test_expire_wait": (ctypes.c_int, [_P, ctypes.c_uint32]),
     "sell_info": (ctypes.c_int, [_P, ctypes.POINTER(sell_info_t)]),
     "sell_export": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "sell_free": (ctypes.c_int, [_P]),
@@ -316,6 +317,12 @@ def sell_check(h: SellMatrix, stream=None):
     """Synchronise the stream; raise SellError(SELL_ETIMEOUT) if a bounded
     device-side wait of the handle's kernels gave up."""
     _check(load().sell_check(h.handle, _stream_ptr(stream)))
+
+
+def sell_test_expire_wait(h: SellMatrix, limit_us: int):
+    """Test hook: the next bulk-staged product's first warp waits limit_us on
+    a barrier nothing completes, so sell_check then reports SELL_ETIMEOUT."""
+    _check(load().sell_test_expire_wait(h.handle, int(limit_us)))
 
 
 def sell_info(h: SellMatrix) -> Info:

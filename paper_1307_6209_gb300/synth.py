@@ -74,13 +74,17 @@ def laplace2d(nx: int, ny: int | None = None) -> CSR:
     return _from_lengths(mask.sum(1), n, cols[mask], vals[mask])
 
 
-def stencil27(n: int, perturb: float = 0.0, seed: int = 0) -> CSR:
+def stencil27(n: int, perturb: float = 0.0, seed: int = 0, rows: int | None = None) -> CSR:
+    """The 27-point stencil on an n^3 grid; with ``rows``, only its first
+    ``rows`` rows (a rows x n^3 matrix whose arrays equal the prefix of the
+    full matrix's, values included)."""
     N = n ** 3
-    idx = np.arange(N, dtype=np.int64)
+    R = N if rows is None else max(0, min(int(rows), N))
+    idx = np.arange(R, dtype=np.int64)
     gx, gy, gz = idx % n, (idx // n) % n, idx // (n * n)
-    cols = np.empty((N, 27), np.int32)
-    mask = np.empty((N, 27), bool)
-    vals = np.empty((N, 27), np.float64)
+    cols = np.empty((R, 27), np.int32)
+    mask = np.empty((R, 27), bool)
+    vals = np.empty((R, 27), np.float64)
     t = 0
     for dz in (-1, 0, 1):
         for dy in (-1, 0, 1):
@@ -97,7 +101,7 @@ def stencil27(n: int, perturb: float = 0.0, seed: int = 0) -> CSR:
     val = vals[mask]
     del vals, mask
     if perturb:
-        rng = np.random.default_rng(seed)
+        rng = np.random.default_rng(seed)  # sequential draws: a prefix of rows gets the prefix of the values
         val *= 1.0 + perturb * rng.uniform(-1.0, 1.0, val.shape[0])
     return _from_lengths(rl, N, col, val)
 
@@ -379,3 +383,13 @@ def long_row_device(N: int, long_len: int, short_len: int = 3, at: int = 0, seed
     rpt = torch.zeros(N + 1, dtype=torch.int64, device=device)
     torch.cumsum(rl, 0, out=rpt[1:])
     return CSR(N, N, rpt, col.to(torch.int32), val)
+
+
+def batch_set(nmat: int = 512, seed: int = 0) -> list:
+    """The batched workload's matrices as (kind, nrows, seed) triples: rows
+    uniform in [1000, 200000]; even positions ``banded`` (bandwidth 64, 7-30
+    entries per row), odd positions ``lognormal``; matrix i uses seed i.
+    Generate each with ``banded_device`` / ``lognormal_device``."""
+    rng = np.random.default_rng(seed)
+    sizes = rng.integers(1000, 200001, nmat)
+    return [("banded" if i % 2 == 0 else "lognormal", int(n), i) for i, n in enumerate(sizes)]

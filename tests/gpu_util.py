@@ -51,3 +51,58 @@ def parity_matrices():
 def oracle_reference(A, x):
     """(y, sum|a x|, row lengths) from the oracle."""
     return oracle.csr_spmv(A, x), oracle.csr_absdot(A, x), A.row_lengths()
+
+
+def rounded_csr(A, store):
+    """A with its values rounded once to the storage type (0 binary64,
+    1 binary32, 2 bfloat16) by the oracle, as binary64: the matrix the kernel
+    actually multiplies."""
+    if store == 0:
+        return A
+    r = oracle.round_values(A.val, store)
+    v = r.astype(np.float64) if store == 1 else oracle.bf16_to_f64(r)
+    return synth.CSR(A.nrows, A.ncols, A.rpt, A.col, v)
+
+
+def host_csr(A):
+    """Host (numpy) copy of a CSR whose arrays may be CUDA tensors."""
+    if isinstance(A.rpt, np.ndarray):
+        return A
+    return synth.CSR(A.nrows, A.ncols, A.rpt.cpu().numpy(), A.col.cpu().numpy(),
+                     A.val.cpu().numpy().astype(np.float64))
+
+
+def assert_oracle_parity(A, store, X, Y, flags=0, Y0=None, what=""):
+    """Every column of a GPU result Y (nrows, or nrows x k) against the
+    oracle's binary64 CRS product (Listing "crs") on the stored values, within
+    the bound of the arithmetic the kernel ran: tol_f64 for binary64 storage,
+    tol_f32 for binary32 chains, tol_dot2 for compensated rows (flags 0x2 on
+    every row, 0x8 on rows of more than 64 entries).  flags 0x1 adds Y0."""
+    X = np.asarray(X, np.float64)
+    Y = np.asarray(Y, np.float64)
+    acc = bool(flags & 0x1)
+    if X.ndim == 1:
+        X, Y = X[:, None], Y[:, None]
+        if Y0 is not None:
+            Y0 = np.asarray(Y0)[:, None]
+    if acc:
+        Y0 = np.asarray(Y0, np.float64)
+    Ar = rounded_csr(A, store)
+    rl = A.row_lengths()
+    n = rl + (1 if acc else 0)
+    for c in range(X.shape[1]):
+        x = X[:, c]
+        ref = oracle.csr_spmv(Ar, x, y0=Y0[:, c] if acc else None, accumulate=acc)
+        scale = oracle.csr_absdot(Ar, x) + (np.abs(Y0[:, c]) if acc else 0.0)
+        if store == 0:
+            tol = tol_f64(n, scale)
+        elif flags & 0x2:
+            tol = tol_dot2(n, scale, ref)
+        elif flags & 0x8:
+            tol = np.where(rl > 64, tol_dot2(n, scale, ref), tol_f32(n, scale))
+        else:
+            tol = tol_f32(n, scale)
+        err = np.abs(Y[:, c] - ref)
+        bad = np.nonzero(~(err <= tol))[0]
+        assert bad.size == 0, (f"{what} column {c}: {bad.size} rows outside the bound, first row {bad[0]}: "
+                               f"got {Y[bad[0], c]!r}, oracle {ref[bad[0]]!r}, tol {tol[bad[0]]!r}")

@@ -134,3 +134,37 @@ def test_binding_refuses_mismatched_buffers():
     Y = torch.zeros((A.nrows, 4), dtype=torch.float64, device="cuda")
     with pytest.raises(ValueError):
         sell.sell_spmmv(h, X[:, ::2], Y)  # every other column: not contiguous along k
+
+
+def test_bounded_device_wait_runs_out_and_is_reported():
+    """The bulk-staged SpMV's failure route, made without a fault: one warp
+    waits (1 ms limit) on a barrier that nothing completes, gives up, drains
+    its own copies and ends; sell_check reports SELL_ETIMEOUT once and clears
+    it, and the next product -- normal limits -- is bitwise the launch-mode-0
+    product again."""
+    import torch
+    from paper_1307_6209_gb300 import sell
+
+    # a banded matrix with no long rows: every warp of the bulk-staged grid
+    # (about five chunks each) stages pieces, the first warp included
+    A = synth.banded(400_000, seed=9)
+    h = sell.sell_build(A, C=32, sigma=1)
+    x = torch.from_numpy(synth.vector(A.ncols, seed=2)).cuda()
+    y0 = torch.empty(A.nrows, dtype=torch.float64, device="cuda")
+    sell.sell_spmv(h, x, y0)
+    assert _status(sell.sell_test_expire_wait, h, 1000) == sell.SELL_EUNSUPPORTED  # launch mode 0
+    sell.sell_set_launch(h, 256, 4, 2)
+    assert _status(sell.sell_test_expire_wait, h, 0) == sell.SELL_EINVAL
+    assert _status(sell.sell_test_expire_wait, h, 2_000_000) == sell.SELL_EINVAL
+    sell.sell_test_expire_wait(h, 1000)
+    y = torch.full((A.nrows,), float("nan"), dtype=torch.float64, device="cuda")
+    sell.sell_spmv(h, x, y)
+    assert _status(sell.sell_check, h) == sell.SELL_ETIMEOUT
+    assert "gave up" in sell.sell_last_error()
+    assert torch.isnan(y).any()  # the rows of the warp that gave up were never written
+    sell.sell_check(h)  # the record was cleared
+    y.fill_(float("nan"))
+    sell.sell_spmv(h, x, y)  # the hook applied to one launch only
+    sell.sell_check(h)
+    assert torch.equal(y, y0)
+    h.free()

@@ -6,7 +6,8 @@ configuration bench.py times (tuned C, sigma, block, unroll):
   product within the binary64 row-wise bound;
 * 27-point stencil on 200^3 (213,847,192 nnz = 598^3): chunk structure and
   row lengths byte for byte, the stored size against its closed form, every
-  y against the oracle; binary32 storage within the binary32 bound.
+  y against the oracle; binary32 and bfloat16 storage within the binary32
+  bound against the oracle on the rounded values.
 """
 import numpy as np
 import pytest
@@ -111,3 +112,16 @@ def test_stencil27_200_full():
     ref32 = oracle.csr_spmv(Ar, x64, nthreads=0)
     scale32 = oracle.csr_absdot(Ar, x64)
     assert np.all(np.abs(y32.cpu().numpy().astype(np.float64) - ref32) <= tol_f32(rl, scale32))
+    h32.free()
+    del Ar, ref32, scale32
+
+    # bfloat16 storage at full size (the benchmark's bf16 stencil), same x
+    hb = sell.sell_build(Ad, C=32, sigma=1, store_type=sell.SELL_BF16)
+    sell.sell_set_launch(hb, 256, 4, 1)
+    sell.sell_spmv(hb, torch.from_numpy(x32).cuda(), y32)
+    torch.cuda.synchronize()
+    Ab = synth.CSR(A.nrows, A.ncols, A.rpt, A.col, oracle.bf16_to_f64(oracle.round_values(A.val, oracle.BF16)))
+    refb = oracle.csr_spmv(Ab, x64, nthreads=0)
+    scaleb = oracle.csr_absdot(Ab, x64)
+    assert np.all(np.abs(y32.cpu().numpy().astype(np.float64) - refb) <= tol_f32(rl, scaleb))
+    hb.free()

@@ -1,6 +1,7 @@
 """Continuous-batching server: every result equals the same request run alone
-(bitwise), requests that arrive while others run are admitted and overlap,
-and the HBM budget is never exceeded."""
+(bitwise) and agrees with the oracle's binary64 CRS product within the bound
+of its storage type, requests that arrive while others run are admitted and
+overlap, and the HBM budget is never exceeded."""
 import threading
 import time
 
@@ -8,17 +9,22 @@ import numpy as np
 import pytest
 
 from paper_1307_6209_gb300 import synth
+from tests.gpu_util import assert_oracle_parity, host_csr
 
 pytestmark = pytest.mark.gpu
 
 
-def _mats(seed=0):
+def _mats(seed=0, hosts=None):
+    """Six resident matrices (binary64 and binary32 storage); with `hosts`, a
+    host copy of each CSR is appended for the oracle."""
     from paper_1307_6209_gb300 import sell
     mats = []
     for i, n in enumerate([3000, 50000, 20000, 120000, 7000, 60000]):
         A = synth.lognormal_device(n, seed=seed + i, cap=800)
         st = sell.SELL_F64 if i % 2 == 0 else sell.SELL_F32
         mats.append(sell.sell_build(A, C=32, sigma=n if i % 3 else 1, store_type=st))
+        if hosts is not None:
+            hosts.append(host_csr(A))
     return mats
 
 
@@ -51,7 +57,8 @@ def _alone(h, X):
 
 def test_results_alone_equal_in_the_mix():
     from paper_1307_6209_gb300 import serving
-    mats = _mats()
+    hosts = []
+    mats = _mats(hosts=hosts)
     srv = serving.Server(mats, hbm_budget_bytes=8 << 30, max_batch=16, streams=3).start()
     rng = np.random.default_rng(1)
     reqs = []
@@ -69,9 +76,14 @@ def test_results_alone_equal_in_the_mix():
     st = srv.stats()
     srv.stop()
     assert st["requests"] == len(reqs) and st["batches"] >= 2
+    ks = set()
     for r, y in zip(reqs, got):
         ref = _alone(mats[r.mid], r.X)
         assert y.numpy().tobytes() == ref.numpy().tobytes(), f"request {r.rid} differs"
+        assert_oracle_parity(hosts[r.mid], mats[r.mid].info.store_type, r.X.numpy(), y.numpy(),
+                             what=f"request {r.rid}")
+        ks.add((mats[r.mid].info.store_type, 1 if r.X.dim() == 1 else r.X.shape[1]))
+    assert {st for st, _ in ks} == {0, 1} and max(k for _, k in ks) >= 6
 
 
 def test_requests_arriving_during_a_batch_share_the_next_launch():
@@ -80,8 +92,12 @@ def test_requests_arriving_during_a_batch_share_the_next_launch():
     alone."""
     import torch
     from paper_1307_6209_gb300 import serving, sell
-    big = sell.sell_build(synth.lognormal_device(2_000_000, seed=5), C=32, sigma=2_000_000)
-    mats = _mats(seed=40) + [big]
+    Abig = synth.lognormal_device(2_000_000, seed=5)
+    big = sell.sell_build(Abig, C=32, sigma=2_000_000)
+    hosts = []
+    mats = _mats(seed=40, hosts=hosts) + [big]
+    hosts.append(host_csr(Abig))
+    del Abig
     srv = serving.Server(mats, hbm_budget_bytes=sum(m.info.device_bytes for m in mats) + (4 << 30),
                          max_batch=64, streams=1)
     Xb = torch.rand((big.info.ncols, 8), dtype=torch.float64).pin_memory()
@@ -91,12 +107,17 @@ def test_requests_arriving_during_a_batch_share_the_next_launch():
     rest = [srv.submit(mid, X, to_host=True) for mid, X in made]
     for r in [first] + rest:
         r.wait(60)
+    ybig = first.result().cpu().clone()
     first.release()
     srv.stop()
     assert max(r.batch for r in rest) > 1, "queued requests did not share a launch"
     assert all(r.t_launch >= first.t_launch for r in rest)
+    assert ybig.numpy().tobytes() == _alone(big, Xb).numpy().tobytes()
+    assert_oracle_parity(hosts[-1], sell.SELL_F64, Xb.numpy(), ybig.numpy(), what="2M-row request")
     for r in rest:
         assert r.Y.numpy().tobytes() == _alone(mats[r.mid], r.X).numpy().tobytes()
+        assert_oracle_parity(hosts[r.mid], mats[r.mid].info.store_type, r.X.numpy(), r.Y.numpy(),
+                             what=f"request {r.rid}")
 
 
 def test_budget_is_respected_and_everything_completes():

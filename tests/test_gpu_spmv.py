@@ -99,6 +99,45 @@ def test_spmv_host_io():
     assert y.tobytes() == _spmv(h, x).tobytes()
 
 
+@pytest.mark.parametrize("k", [1, 4, 8])
+@pytest.mark.parametrize("accumulate", [False, True])
+def test_spmmv_host_io_leading_dimensions(k, accumulate):
+    """HOST_IO SpMMV with padded rows (ldx = ldy = k + 3) in pinned host
+    memory: only the k used columns of X are read and of Y written -- the
+    padding columns keep the caller's values -- every column matches the
+    oracle within the binary64 bound, and the result equals the same product
+    on device buffers bit for bit."""
+    import torch
+    from paper_1307_6209_gb300 import sell
+
+    A = synth.lognormal(7001, seed=30 + k, cap=700)  # long rows use the segment scratch too
+    h = sell.sell_build(A, C=32, sigma=4096)
+    ld = k + 3
+    X = synth.block(A.ncols, k, seed=7)
+    Y0 = synth.block(A.nrows, k, seed=8)
+    Xh = torch.full((A.ncols, ld), 7.0, dtype=torch.float64).pin_memory()
+    Xh[:, :k] = torch.from_numpy(X)
+    Yh = torch.full((A.nrows, ld), -3.25, dtype=torch.float64).pin_memory()
+    if accumulate:
+        Yh[:, :k] = torch.from_numpy(Y0)
+    fl = sell.SELL_SPMV_HOST_IO | (sell.SELL_SPMV_ACCUMULATE if accumulate else 0)
+    sell.sell_spmmv(h, Xh[:, :k], Yh[:, :k], flags=fl)
+    torch.cuda.synchronize()
+    got = Yh.numpy()
+    assert np.all(got[:, k:] == -3.25), "padding columns of Y were written"
+    ref = oracle.csr_spmmv(A, X, Y0=Y0 if accumulate else None, accumulate=accumulate)
+    rl = A.row_lengths()
+    for c in range(k):
+        scale = oracle.csr_absdot(A, X[:, c]) + (np.abs(Y0[:, c]) if accumulate else 0.0)
+        assert np.all(np.abs(got[:, c] - ref[:, c]) <= tol_f64(rl + (1 if accumulate else 0), scale)), f"col {c}"
+    Xd = torch.from_numpy(X).cuda()
+    Yd = torch.from_numpy(Y0).cuda() if accumulate else torch.empty((A.nrows, k), dtype=torch.float64,
+                                                                     device="cuda")
+    sell.sell_spmmv(h, Xd, Yd, flags=fl & ~sell.SELL_SPMV_HOST_IO)
+    torch.cuda.synchronize()
+    assert np.ascontiguousarray(got[:, :k]).tobytes() == Yd.cpu().numpy().tobytes()
+
+
 def test_spmv_host_io_alternating_streams():
     """HOST_IO calls that alternate two streams (the overlapped end-to-end
     pattern): every call's y is bitwise the device-buffer product of its own

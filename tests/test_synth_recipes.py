@@ -68,6 +68,19 @@ def test_stencil27_perturbation_bounds():
     assert np.all((r >= 1 - p) & (r <= 1 + p)) and np.std(r) > p / 4
 
 
+def test_stencil27_row_prefix_equals_the_full_matrix():
+    """The reference arm's row sample: the first r rows of the stencil,
+    values included, are the prefix of the full matrix's arrays."""
+    full = synth.stencil27(9, perturb=0.1, seed=3)
+    for r in (0, 1, 80, 400, 729, 10 ** 6):
+        P = synth.stencil27(9, perturb=0.1, seed=3, rows=r)
+        m = min(r, full.nrows)
+        assert P.nrows == m and P.ncols == full.ncols
+        assert np.array_equal(P.rpt, full.rpt[:m + 1])
+        assert np.array_equal(P.col, full.col[:full.rpt[m]])
+        assert np.array_equal(P.val, full.val[:full.rpt[m]])
+
+
 @pytest.mark.parametrize("n", [1, 4, 7])
 def test_stencil27_device_matches_host_structure(n):
     A = synth.stencil27(n)

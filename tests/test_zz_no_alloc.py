@@ -12,9 +12,8 @@ import ctypes
 import numpy as np
 import pytest
 
-import oracle
 from paper_1307_6209_gb300 import synth
-from tests.gpu_util import tol_dot2, tol_f64
+from tests.gpu_util import assert_oracle_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -68,9 +67,8 @@ def test_noalloc_matches_spmmv_twice(k, pad):
             ref, new = Yref[:, :k].cpu().numpy(), Ynew[:, :k].cpu().numpy()
             if pad:
                 assert torch.isnan(Ynew[:, k:]).all()
-        for c in range(k):
-            scale = oracle.csr_absdot(A, X[:, c])
-            assert np.all(np.abs(new[:, c] - ref[:, c]) <= tol_f64(A.row_lengths(), scale))
+        # against the oracle's binary64 CRS product, within the binary64 bound
+        assert_oracle_parity(A, sell.SELL_F64, X, new, what=f"call {call}")
         # the same per-row arithmetic runs in both entry points
         assert new.tobytes() == ref.tobytes()
 
@@ -89,9 +87,10 @@ def test_noalloc_compensated_f32_twice():
         sell.sell_spmv(h, x, yr, flags=fl)
         assert _noalloc(h, x, yn, flags=fl) == sell.SELL_OK, sell.sell_last_error()
         torch.cuda.synchronize()
-        ref, new = yr.cpu().numpy().astype(np.float64), yn.cpu().numpy().astype(np.float64)
-        scale = oracle.csr_absdot(A, x.cpu().numpy().astype(np.float64)) + np.abs(y0.cpu().numpy())
-        assert np.all(np.abs(new - ref) <= 2 * tol_dot2(A.row_lengths() + 1, scale, ref))
+        ref, new = yr.cpu().numpy(), yn.cpu().numpy()
+        # against the oracle on the binary32-rounded values, within the Dot2 bound
+        assert_oracle_parity(A, sell.SELL_F32, x.cpu().numpy(), new, flags=fl, Y0=y0.cpu().numpy(),
+                             what=f"call {call}")
         assert new.tobytes() == ref.tobytes()
 
 
@@ -126,3 +125,18 @@ def test_noalloc_rejects_what_it_cannot_do():
     assert _noalloc(hs, xs, yb) == sell.SELL_OK, sell.sell_last_error()
     torch.cuda.synchronize()
     assert torch.equal(ya, yb)
+    assert_oracle_parity(S, sell.SELL_F64, xs.cpu().numpy(), yb.cpu().numpy(), what="40000 rows of 65")
+    # eight columns do not fit there (the array holds four): the columns run
+    # in narrower blocks, and k = 5 with padded rows leaves the padding alone
+    for k, pad in ((8, 0), (5, 3)):
+        X = synth.block(S.ncols, k, seed=40 + k)
+        Xd = torch.full((S.ncols, k + pad), 9.0, dtype=torch.float64, device="cuda")
+        Xd[:, :k] = torch.from_numpy(X).cuda()
+        Yr = torch.full((S.nrows, k + pad), -1.5, dtype=torch.float64, device="cuda")
+        Yn = Yr.clone()
+        sell.sell_spmmv(hs, Xd[:, :k], Yr[:, :k])
+        assert _noalloc(hs, Xd[:, :k], Yn[:, :k]) == sell.SELL_OK, sell.sell_last_error()
+        torch.cuda.synchronize()
+        assert Yn.cpu().numpy().tobytes() == Yr.cpu().numpy().tobytes()
+        assert torch.all(Yn[:, k:] == -1.5)
+        assert_oracle_parity(S, sell.SELL_F64, X, Yn[:, :k].cpu().numpy(), what=f"k={k}")
