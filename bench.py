@@ -66,6 +66,9 @@ def parse_args():
     p.add_argument("--no-sweep", action="store_true")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--no-extras", action="store_true", help="skip every section but the headline")
+    p.add_argument("--shard", choices=["replicas", "rows"], default="replicas",
+                   help="replicas: every rank multiplies its own copy (weak scaling); rows: the ranks split one "
+                        "matrix by rows, one allgather of x per step (strong scaling)")
     return p.parse_args()
 
 
@@ -1119,10 +1122,93 @@ def run_ours(args):
     return 0
 
 
+def run_sharded(args):
+    """One matrix split by rows over the ranks (dist.shard_rows: whole sorting
+    windows and chunks per rank).  A step is one distributed SpMV: the
+    allgather of x (NCCL), then every rank's own rows; the job's rate is the
+    global flops over the slowest rank's time (strong scaling)."""
+    import torch
+    from paper_1307_6209_gb300 import build as cuda_build
+    from paper_1307_6209_gb300 import dist as sdist
+    from paper_1307_6209_gb300 import model, sell, synth
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    cuda_build.build()
+    sell.load()
+    W = workload(args)
+    C, sigma = args.C or 128, args.sigma or 1
+    stream = torch.cuda.Stream()
+    peak, peak_src = load_peaks()
+    with torch.cuda.stream(stream):
+        A = W["device"]() if W["device"] is not None else to_device(W["host"]())
+        N, nnz = int(A.nrows), int(A.rpt[-1])
+        bounds = sdist.shard_rows(N, sigma, C, ws, rpt=A.rpt.cpu().numpy())
+        shard = sdist.build_shard(A, bounds, rank, C=C, sigma=sigma, stream=stream)
+        del A
+        torch.cuda.empty_cache()
+        sell.sell_set_launch(shard.handle, args.block or 128, args.unroll or 4,
+                             args.pipeline if args.pipeline is not None else 1)
+        r0, r1 = shard.rows
+        x = torch.from_numpy(synth.vector(N, seed=0)).cuda()
+        x_local = x[r0:r1].contiguous()
+        del x
+        y_local = torch.empty(r1 - r0, dtype=torch.float64, device="cuda")
+        gather = (lambda xl: xl) if ws == 1 else None
+
+        def step():
+            sdist.sharded_spmv(shard, x_local, y_local, gather=gather, stream=stream)
+        for _ in range(args.warmup):
+            step()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t_start.record(stream)
+        for a, b in ev:
+            a.record(stream)
+            step()
+            b.record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    total_s = t_start.elapsed_time(t_end) * 1e-3
+    step_s = sdist.max_over_ranks(total_s, device="cuda") / args.steps
+    loc_s = sum(a.elapsed_time(b) for a, b in ev) * 1e-3 / args.steps
+    inf = shard.handle.info
+    alg = model.algorithmic_bytes(inf.nrows, inf.ncols, inf.nnz, inf.nchunks, C, 8, 8, inf.has_perm)
+    if rank == 0:
+        value = 2.0 * nnz / step_s / 1e9
+        line = {"metric": METRIC, "value": round(value, 2), "unit": "GF/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": round(step_s * 1e3, 5), "higher_is_better": True,
+                "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": W["desc"], "C": C, "sigma": sigma, "nrows": N, "nnz": nnz,
+                           "parallelism": f"rows x{ws} (allgather of x, then the local rows)",
+                           "rank0_rows": [r0, r1]},
+                "roofline": {"bound": "hbm", "achieved": round(alg / loc_s / 1e9, 1), "peak": peak, "unit": "GB/s",
+                             "frac": round(alg / loc_s / 1e9 / peak, 4), "traffic": None,
+                             "peak_source": peak_src,
+                             "note": "rank 0's step (allgather + local SpMV) against its local algorithmic bytes"},
+                "cpu_baseline": None, "e2e": None, "gpu_launches": args.steps}
+        print(json.dumps(line), flush=True)
+    shard.handle.free()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.shard == "rows":
+        return run_sharded(args)
     return run_ours(args)
 
 

@@ -159,6 +159,14 @@ SELL_API sell_status sell_build(const sell_csr *A, const sell_opts *opts, void *
                                           SELL_SPMV_COMPENSATED takes precedence */
 #define SELL_SPMV_COMPENSATED 0x2u  /* F32/BF16 storage: compensated (Dot2)
                                        binary32 accumulation of each row */
+#define SELL_SPMV_RHS_BLOCK4 0x10u  /* SpMMV and batch items: multiply the right-hand
+                                       sides in blocks of at most 4 (default 8);
+                                       one of RHS_BLOCK4/2/1, the smallest wins.
+                                       A tuning knob: every column keeps its own
+                                       per-row operation order, so the results
+                                       are the same bits for any block width */
+#define SELL_SPMV_RHS_BLOCK2 0x20u  /* ... at most 2 */
+#define SELL_SPMV_RHS_BLOCK1 0x40u  /* ... one at a time */
 #define SELL_SPMV_HOST_IO 0x4u      /* x and y (X and Y) are host pointers
                                        (pinned for asynchronous copies); the
                                        copies to and from the handle's two
@@ -325,6 +333,13 @@ SELL_API sell_status sell_batch_create(const sell_batch_item *items, int32_t n, 
 /* Launch a plan on `stream` (kernel launches only: capturable in a CUDA
  * graph).  grid must be 0 (reserved).  Errors: SELL_EINVAL, SELL_ECUDA. */
 SELL_API sell_status sell_batch_run(sell_batch_plan plan, int32_t grid, void *stream);
+
+/* Launch tuning of a plan (autotuner knob): `block` threads per block, 64,
+ * 128 or 256 (the default), and as many sorted rows (or long-row segment
+ * threads) per work unit.  The results do not depend on it.  Takes effect
+ * at the next sell_batch_run (a graph captured before keeps the old launch).
+ * Errors: SELL_EINVAL, SELL_EUNSUPPORTED (too many units). */
+SELL_API sell_status sell_batch_set_launch(sell_batch_plan plan, int32_t block);
 
 /* Release a plan (NULL accepted).  The memory is returned stream-ordered on
  * the stream of the plan's latest sell_batch_run (no host wait); a plan run

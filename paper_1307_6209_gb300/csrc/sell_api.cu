@@ -189,7 +189,7 @@ sell_status sell_spmmv(sell_handle h, const void *X, int64_t ldx, void *Y, int64
                        uint32_t flags, void *stream) {
     if (!h) return fail(SELL_EINVAL, "sell_spmmv: NULL handle");
     if (k < 1 || ldx < k || ldy < k) return fail(SELL_EINVAL, "sell_spmmv: need k >= 1, ldx >= k, ldy >= k");
-    if (flags & ~(SELL_SPMV_ACCUMULATE | kCompFlags | SELL_SPMV_HOST_IO))
+    if (flags & ~(SELL_SPMV_ACCUMULATE | kCompFlags | kRhsFlags | SELL_SPMV_HOST_IO))
         return fail(SELL_EINVAL, "sell_spmmv: unknown flags");
     if ((flags & kCompFlags) && h->store_type == SELL_F64)
         return fail(SELL_EUNSUPPORTED, "compensated accumulation needs F32/BF16 storage");
@@ -389,6 +389,11 @@ sell_status sell_batch_create(const sell_batch_item *items, int32_t n, void *str
 sell_status sell_batch_run(sell_batch_plan plan, int32_t grid, void *stream) {
     if (!plan || grid < 0) return fail(SELL_EINVAL, "sell_batch_run: bad arguments");
     return batch_run(plan, grid, static_cast<cudaStream_t>(stream));
+}
+
+sell_status sell_batch_set_launch(sell_batch_plan plan, int32_t block) {
+    if (!plan) return fail(SELL_EINVAL, "sell_batch_set_launch: NULL plan");
+    return batch_set_tile(plan, block);
 }
 
 sell_status sell_batch_free(sell_batch_plan plan) {

@@ -1,12 +1,14 @@
 // sell_batch.cu -- many SELL-C-sigma products in persistent launches.
 //
 // A plan splits every product into column blocks of 8, 4, 2 or 1 right-hand
-// sides and groups the blocks by kernel variant (value type, block width,
+// sides (at most the item's SELL_SPMV_RHS_BLOCK* width) and groups the blocks
+// by kernel variant (value type, block width,
 // plain or compensated accumulation).  Each variant present gets one launch
 // (per 160 products): its products and the block ranges of their work units
-// travel in the kernel's parameter space -- a unit is kTileRows sorted rows
-// of one product (its short rows), or kTileRows threads of the product's
-// long-row segment units.  Creating a plan makes one device allocation (the
+// travel in the kernel's parameter space -- a unit is one block's worth of
+// sorted rows of one product (its short rows; kTileRows = 256 by default,
+// 64 or 128 after sell_batch_set_launch), or as many threads of the
+// product's long-row segment units.  Creating a plan makes one device allocation (the
 // products' long-row scratch) and no copies, and does not synchronise.  One
 // block per unit, long-row units first and biggest products first; the
 // hardware block scheduler balances the uneven products.  (A grid-stride "persistent" form of this kernel was measured:
@@ -54,8 +56,8 @@ struct Prod {
 // register footprint at that of the single-product kernel.  The work units
 // need no table: block w belongs to range i of `start` (start[i] <= w <
 // start[i+1]); ranges 0..nprod-1 are the products' long-row units
-// (kTileRows segment threads per block), ranges nprod..2*nprod-1 their short
-// rows (kTileRows rows per block).
+// (blockDim.x segment threads per block), ranges nprod..2*nprod-1 their short
+// rows (blockDim.x rows per block).
 constexpr int kLaunchProds = 160;  // 160 * 168 B + the ranges fit the 32 KB parameter limit
 
 struct LaunchParams {
@@ -81,7 +83,7 @@ __device__ __forceinline__ void batch_unit(const LaunchParams &lp) {
     }
     const bool is_long = lo < lp.nprod;
     const Prod &P = lp.prods[is_long ? lo : lo - lp.nprod];
-    const int64_t first = (int64_t)(w - lp.start[lo]) * kTileRows;
+    const int64_t first = (int64_t)(w - lp.start[lo]) * blockDim.x;
     if (is_long) {
         const int64_t v = first + threadIdx.x;
         if (v < P.long_threads)
@@ -152,17 +154,16 @@ KernelFn kernel_for(int type, int comp, int kb) {
 
 namespace {
 size_t up256(size_t x) { return (x + 255) / 256 * 256; }
-int block_width(int rem) { return rem >= 8 ? 8 : rem >= 4 ? 4 : rem >= 2 ? 2 : 1; }
 }  // namespace
 
 // Long-row scratch of one batch item (all its column blocks): the segment
 // partials of every block, then the counters of every block (cleared
 // together).  0 for matrices without long rows.
-size_t batch_item_scratch(const sell_matrix *h, int32_t k, size_t *counter_offset) {
+size_t batch_item_scratch(const sell_matrix *h, int32_t k, uint32_t flags, size_t *counter_offset) {
     size_t pb = 0, cb = 0;
     if (h->nunits > 0 && h->nrows > 0) {
         for (int32_t done = 0; done < k;) {
-            const int kb = block_width(k - done);
+            const int kb = rhs_block(k - done, max_rhs_block(flags));
             pb += up256((size_t)h->nunits * h->C * kb * 8);
             cb += up256((size_t)(h->nlong + h->nunits) * h->C * sizeof(int32_t));
             done += kb;
@@ -171,6 +172,26 @@ size_t batch_item_scratch(const sell_matrix *h, int32_t k, size_t *counter_offse
     if (counter_offset) *counter_offset = pb;
     return pb + cb;
 }
+
+namespace {
+// The block ranges of a launch's products for blocks of `tile` threads:
+// long-row units of every product first, then their short rows.  Returns the
+// number of blocks.
+int64_t assign_units(LaunchParams *lp, int tile) {
+    const int np = lp->nprod;
+    int64_t w = 0;
+    for (int j = 0; j < np; ++j) {
+        lp->start[j] = (int32_t)std::min<int64_t>(w, 0x7FFFFFFF);
+        w += (lp->prods[j].long_threads + tile - 1) / tile;
+    }
+    for (int j = 0; j < np; ++j) {
+        lp->start[np + j] = (int32_t)std::min<int64_t>(w, 0x7FFFFFFF);
+        w += (lp->prods[j].N + tile - 1) / tile;
+    }
+    lp->start[2 * np] = (int32_t)std::min<int64_t>(w, 0x7FFFFFFF);
+    return w;
+}
+}  // namespace
 
 sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s, sell_batch *b,
                          void *const *scratch) {
@@ -184,7 +205,7 @@ sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s
     if (!scratch) {
         size_t total = 0;
         for (int32_t i = 0; i < n; ++i)
-            if (items[i].A && items[i].k >= 1) total += batch_item_scratch(items[i].A, items[i].k, nullptr);
+            if (items[i].A && items[i].k >= 1) total += batch_item_scratch(items[i].A, items[i].k, items[i].flags, nullptr);
         if (total > 0) {
             own = static_cast<char *>(b->al.get(total, s));
             if (!own) return fail(SELL_ENOMEM, "sell_batch_create: segment scratch allocation failed");
@@ -199,13 +220,13 @@ sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s
         if (it.k < 1 || it.ldx < it.k || it.ldy < it.k)
             return fail(SELL_EINVAL, "sell_batch_create: need k >= 1, ldx >= k, ldy >= k");
         if (h->nrows > 0 && (!it.X || !it.Y)) return fail(SELL_EINVAL, "sell_batch_create: NULL X/Y");
-        if (it.flags & ~(SELL_SPMV_ACCUMULATE | kCompFlags))
+        if (it.flags & ~(SELL_SPMV_ACCUMULATE | kCompFlags | kRhsFlags))
             return fail(SELL_EINVAL, "sell_batch_create: unsupported flags");
         if ((it.flags & kCompFlags) && h->store_type == SELL_F64)
             return fail(SELL_EUNSUPPORTED, "compensated accumulation needs F32/BF16 storage");
         if (h->nrows == 0) continue;
         size_t coff = 0;
-        const size_t sbytes = batch_item_scratch(h, it.k, &coff);
+        const size_t sbytes = batch_item_scratch(h, it.k, it.flags, &coff);
         char *sc = nullptr;
         if (sbytes > 0) {
             sc = scratch ? static_cast<char *>(scratch[i]) : own + own_off;
@@ -216,7 +237,7 @@ sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s
         size_t poff = 0, cpos = coff;
         const size_t xs = h->store_type == SELL_F64 ? 8 : 4;
         for (int32_t done = 0; done < it.k;) {
-            const int kb = block_width(it.k - done);
+            const int kb = rhs_block(it.k - done, max_rhs_block(it.flags));
             Prod P;
             P.val = h->val;
             P.col = h->col;
@@ -289,18 +310,8 @@ sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s
             auto *lp = new (std::nothrow) LaunchParams();
             if (!lp) return fail(SELL_ENOMEM, "sell_batch_create: host allocation failed");
             lp->nprod = np;
-            int64_t w = 0;
-            for (int j = 0; j < np; ++j) {  // long-row units of every product first
-                const Prod &P = prods[ids[p0 + j]];
-                lp->prods[j] = P;
-                lp->start[j] = (int32_t)w;
-                w += (P.long_threads + kTileRows - 1) / kTileRows;
-            }
-            for (int j = 0; j < np; ++j) {  // then their short rows
-                lp->start[np + j] = (int32_t)w;
-                w += (prods[ids[p0 + j]].N + kTileRows - 1) / kTileRows;
-            }
-            lp->start[2 * np] = (int32_t)w;
+            for (int j = 0; j < np; ++j) lp->prods[j] = prods[ids[p0 + j]];
+            const int64_t w = assign_units(lp, b->tile);
             if (w > 0x7FFFFFFF) {
                 delete lp;
                 return fail(SELL_EUNSUPPORTED, "sell_batch_create: too many work units in one launch");
@@ -328,13 +339,35 @@ void batch_release(sell_batch *b, cudaStream_t s) {
     b->scratch.clear();
 }
 
+sell_status batch_set_tile(sell_batch *b, int32_t tile) {
+    if (tile != 64 && tile != 128 && tile != 256)
+        return fail(SELL_EINVAL, "sell_batch_set_launch: block must be 64, 128 or 256");
+    std::vector<int64_t> ws;
+    for (const sell_batch::Group &G : b->groups) {
+        LaunchParams tmp = *static_cast<const LaunchParams *>(G.params);
+        const int64_t w = assign_units(&tmp, tile);
+        if (w > 0x7FFFFFFF) return fail(SELL_EUNSUPPORTED, "sell_batch_set_launch: too many work units in one launch");
+        ws.push_back(w);
+    }
+    b->tile = tile;
+    b->nwork = 0;
+    for (size_t g = 0; g < b->groups.size(); ++g) {
+        sell_batch::Group &G = b->groups[g];
+        assign_units(static_cast<LaunchParams *>(G.params), tile);
+        G.nwork = ws[g];
+        G.grid = (int32_t)ws[g];
+        b->nwork += ws[g];
+    }
+    return SELL_OK;
+}
+
 sell_status batch_run(sell_batch *b, int32_t grid, cudaStream_t s) {
     if (grid != 0) return fail(SELL_EINVAL, "sell_batch_run: grid must be 0 (one block per work unit)");
     b->last_stream = s;
     b->ran = true;
     for (const sell_batch::Group &G : b->groups) {
         KernelFn fn = reinterpret_cast<KernelFn>(G.fn);
-        fn<<<G.grid, kTileRows, 0, s>>>(*static_cast<const LaunchParams *>(G.params));
+        fn<<<G.grid, b->tile, 0, s>>>(*static_cast<const LaunchParams *>(G.params));
         SELL_CUDA_TRY(cudaGetLastError());
     }
     return SELL_OK;

@@ -65,6 +65,22 @@ inline int comp_mode(uint32_t flags) {
     return (flags & SELL_SPMV_COMPENSATED_LONG) ? 2 : 0;
 }
 constexpr uint32_t kCompFlags = SELL_SPMV_COMPENSATED | SELL_SPMV_COMPENSATED_LONG;
+constexpr uint32_t kRhsFlags = SELL_SPMV_RHS_BLOCK4 | SELL_SPMV_RHS_BLOCK2 | SELL_SPMV_RHS_BLOCK1;
+
+// The widest block of right-hand sides the flags allow (8 by default).
+inline int max_rhs_block(uint32_t flags) {
+    if (flags & SELL_SPMV_RHS_BLOCK1) return 1;
+    if (flags & SELL_SPMV_RHS_BLOCK2) return 2;
+    return (flags & SELL_SPMV_RHS_BLOCK4) ? 4 : 8;
+}
+
+// The next block of right-hand sides: the widest of 8, 4, 2, 1 that fits the
+// remaining columns and the flags' limit.
+inline int rhs_block(int rem, int maxw) {
+    int kb = rem >= 8 ? 8 : rem >= 4 ? 4 : rem >= 2 ? 2 : 1;
+    while (kb > maxw) kb >>= 1;
+    return kb;
+}
 
 }  // namespace sell
 
@@ -132,6 +148,7 @@ struct sell_batch {
     std::vector<Group> groups;
     int64_t nwork = 0;
     int32_t nprod = 0;
+    int32_t tile = 256;  // threads per block = rows (or segment threads) per work unit
     cudaStream_t last_stream = nullptr;  // stream of the latest sell_batch_run
     bool ran = false;
 };
@@ -153,8 +170,9 @@ sell_status launch_dot(sell_matrix *h, const void *x, const void *y, double *out
 // items without long rows); NULL: the plan allocates its own.
 sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s, sell_batch *b,
                          void *const *scratch = nullptr);
-size_t batch_item_scratch(const sell_matrix *h, int32_t k, size_t *counter_offset);
+size_t batch_item_scratch(const sell_matrix *h, int32_t k, uint32_t flags, size_t *counter_offset);
 sell_status batch_run(sell_batch *b, int32_t grid, cudaStream_t s);
+sell_status batch_set_tile(sell_batch *b, int32_t tile);
 void batch_release(sell_batch *b, cudaStream_t s);
 sell_status bench_read(const void *buf, size_t bytes, double *sink, int32_t grid, cudaStream_t s);
 sell_status bench_fma64(double *sink, int32_t grid, int32_t iters, cudaStream_t s);

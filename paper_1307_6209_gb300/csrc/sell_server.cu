@@ -107,7 +107,7 @@ void sizes(const sell_server *S, Req *r) {
     const size_t es = h->store_type == SELL_F64 ? 8 : 4;
     r->xb = (size_t)h->ncols * r->k * es;
     r->yb = (size_t)h->nrows * r->k * es;
-    r->sb = batch_item_scratch(h, r->k, nullptr);
+    r->sb = batch_item_scratch(h, r->k, r->flags, nullptr);
 }
 
 // Work of a request: stored elements times right-hand sides.

@@ -32,14 +32,16 @@ cudaError_t dispatch(const sell_matrix *h, const void *X, int64_t ldx, void *Y, 
 
 }  // namespace
 
-// Splits k into kernel blocks of 8, 4, 2, 1 columns (every column keeps the
-// same per-row operation order, so the split does not change any result).
-// The segment scratch grows on the first product with a wider block.
+// Splits k into kernel blocks of 8, 4, 2, 1 columns, at most the flags' block
+// width (every column keeps the same per-row operation order, so the split
+// does not change any result).  The segment scratch grows on the first
+// product with a wider block.
 sell_status launch_spmmv(sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy,
                          int32_t k, uint32_t flags, cudaStream_t s) {
     if (h->nrows == 0) return SELL_OK;
+    const int maxw = max_rhs_block(flags);
     if (h->nunits > 0) {
-        const int need = k >= 8 ? 8 : k >= 4 ? 4 : k >= 2 ? 2 : 1;
+        const int need = rhs_block(k, maxw);
         if (need > h->part_k) {
             void *p = h->al.get((size_t)h->nunits * h->C * need * 8, s);
             if (!p) return fail(SELL_ENOMEM, "segment scratch allocation failed");
@@ -53,8 +55,7 @@ sell_status launch_spmmv(sell_matrix *h, const void *X, int64_t ldx, void *Y, in
     const size_t xs = h->store_type == SELL_F64 ? 8 : 4;
     int32_t done = 0;
     while (done < k) {
-        int rem = k - done;
-        int kb = rem >= 8 ? 8 : rem >= 4 ? 4 : rem >= 2 ? 2 : 1;
+        const int kb = rhs_block(k - done, maxw);
         const char *Xb = static_cast<const char *>(X) + (size_t)done * xs;
         char *Yb = static_cast<char *>(Y) + (size_t)done * xs;
         int vec = (((uintptr_t)Xb % 16) == 0 && ((ldx * xs) % 16) == 0) ? 1 : 0;

@@ -25,6 +25,9 @@ SELL_SPMV_ACCUMULATE = 0x1
 SELL_SPMV_COMPENSATED = 0x2
 SELL_SPMV_HOST_IO = 0x4
 SELL_SPMV_COMPENSATED_LONG = 0x8
+SELL_SPMV_RHS_BLOCK4 = 0x10
+SELL_SPMV_RHS_BLOCK2 = 0x20
+SELL_SPMV_RHS_BLOCK1 = 0x40
 
 DTYPE_NAMES = {SELL_F64: "f64", SELL_F32: "f32", SELL_BF16: "bf16"}
 VALUE_BYTES = {SELL_F64: 8, SELL_F32: 4, SELL_BF16: 2}
@@ -105,6 +108,7 @@ SIGNATURES = {
                                          ctypes.POINTER(_P)]),
     "sell_batch_run": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
     "sell_batch_free": (ctypes.c_int, [_P]),
+    "sell_batch_set_launch": (ctypes.c_int, [_P, ctypes.c_int32]),
     "sell_server_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.POINTER(sell_server_opts),
                                           ctypes.POINTER(_P)]),
     "sell_server_submit": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32, _P, ctypes.c_uint32,
@@ -367,6 +371,10 @@ class BatchPlan:
 
     def run(self, grid: int = 0, stream=None):
         _check(load().sell_batch_run(self.handle, int(grid), _stream_ptr(stream)))
+
+    def set_launch(self, block: int):
+        """Threads per block (64, 128, 256): rows per work unit."""
+        _check(load().sell_batch_set_launch(self.handle, int(block)))
 
     def free(self):
         if self.handle and self.handle.value:

@@ -3,8 +3,10 @@
 * Weak scaling (what bench.py does under torchrun): the job throughput is the
   sum of the ranks' work over the slowest rank's time.
 * Row sharding of one matrix: the ranks' formats are exactly the pieces of
-  the global format (no sorting window or chunk crosses a boundary), and after
-  one allgather of x each rank's rows give the global product bit for bit.
+  the global format (no sorting window or chunk crosses a boundary), and
+  dist.sharded_spmv -- one allgather of x over gloo, then the rank's own rows,
+  here with the oracle's Listing "sell" as the local product -- gives the
+  global product bit for bit.
 """
 import os
 import socket
@@ -41,8 +43,7 @@ def _worker(rank, world, port, results):
         C, sigma = 32, 256
         bounds = sdist.shard_rows(A.nrows, sigma, C, world, rpt=A.rpt)
         r0, r1 = bounds[rank]
-        S = synth.CSR(r1 - r0, A.ncols, A.rpt[r0:r1 + 1] - A.rpt[r0], A.col[A.rpt[r0]:A.rpt[r1]],
-                      A.val[A.rpt[r0]:A.rpt[r1]])
+        S = sdist.slice_rows(A, r0, r1)
         Fs = oracle.sell_build(S, C, sigma)
         F = oracle.sell_build(A, C, sigma)
         c0, c1 = r0 // C, r0 // C + Fs["nchunks"]
@@ -52,15 +53,18 @@ def _worker(rank, world, port, results):
             and np.array_equal(Fs["col"], F["col"][F["cs"][c0]:F["cs"][c1]])
             and np.array_equal(Fs["perm"] + r0, F["perm"][r0:r1]))
 
-        # one allgather of x (each rank owns the slice matching its rows)
+        # the package's sharded product: each rank owns the slice of x
+        # matching its rows; one allgather, then the local rows
         mine = torch.from_numpy(x[r0:r1].copy())
+        shard = sdist.RowShard(bounds, rank)
+        seen = {}
+
+        def local_product(xg, _y):
+            seen["x"] = xg.numpy().tobytes() == x.tobytes()
+            return torch.from_numpy(oracle.sell_spmv(Fs, xg.numpy()))
+        y_local = sdist.sharded_spmv(shard, mine, product=local_product).numpy()
+        out["x_gathered"] = seen["x"]
         width = max(b - a for a, b in bounds)
-        pad = torch.zeros(width, dtype=torch.float64)
-        pad[:mine.numel()] = mine
-        parts = [torch.empty(width, dtype=torch.float64) for _ in range(world)]
-        dist.all_gather(parts, pad)
-        xg = torch.cat([p[:b - a] for p, (a, b) in zip(parts, bounds)]).numpy()
-        y_local = oracle.sell_spmv(Fs, xg)
         ypad = torch.zeros(width, dtype=torch.float64)
         ypad[:y_local.shape[0]] = torch.from_numpy(y_local)
         yparts = [torch.empty(width, dtype=torch.float64) for _ in range(world)]
@@ -85,6 +89,7 @@ def test_ranks_gloo(world):
         # units 100, 200, ... over the slowest rank's 0.5 + (world - 1) seconds
         assert res[r]["tp"] == pytest.approx(100.0 * world * (world + 1) / 2 / (0.5 + world - 1))
         assert res[r]["pieces"], f"rank {r}: shard format is not a piece of the global format"
+        assert res[r]["x_gathered"], f"rank {r}: the allgather did not rebuild x"
         assert res[r]["y_equal"], f"rank {r}: sharded product differs"
     b = res[0]["bounds"]
     assert b[0][0] == 0 and b[-1][1] == 5003 and all(x % 256 == 0 for x, _ in b)

@@ -2,20 +2,16 @@
 
 dist.shard_rows cuts the rows at multiples of lcm(min(sigma, N), C), so no
 sorting window and no chunk crosses a shard: each shard's GPU format must be
-exactly the matching piece of the global format, and with the full x (what
-one allgather gives every rank) the shards' y slices must concatenate to the
-global y bit for bit."""
+exactly the matching piece of the global format, and dist.sharded_spmv --
+with the full x that one allgather gives every rank, here handed over by its
+gather seam since the shards share one process -- must give y slices that
+concatenate to the global y bit for bit."""
 import numpy as np
 import pytest
 
 from paper_1307_6209_gb300 import synth
 
 pytestmark = pytest.mark.gpu
-
-
-def _slice(A, r0, r1):
-    return synth.CSR(r1 - r0, A.ncols, A.rpt[r0:r1 + 1] - A.rpt[r0], A.col[A.rpt[r0]:A.rpt[r1]],
-                     A.val[A.rpt[r0]:A.rpt[r1]])
 
 
 @pytest.mark.parametrize("world", [2, 3, 5])
@@ -32,9 +28,10 @@ def test_shards_are_pieces_and_concatenate_bitwise(world, C, sigma):
     yg = torch.empty(A.nrows, dtype=torch.float64, device="cuda")
     sell.sell_spmv(hg, x, yg)
     parts = []
-    for r0, r1 in sdist.shard_rows(A.nrows, sigma, C, world, rpt=A.rpt):
-        S = _slice(A, r0, r1)
-        hs = sell.sell_build(S, C=C, sigma=sigma)
+    bounds = sdist.shard_rows(A.nrows, sigma, C, world, rpt=A.rpt)
+    for rank, (r0, r1) in enumerate(bounds):
+        shard = sdist.build_shard(A, bounds, rank, C=C, sigma=sigma)
+        hs = shard.handle
         F = sell.sell_export(hs)
         c0, c1 = r0 // C, r0 // C + hs.info.nchunks
         assert np.array_equal(F["cs"], G["cs"][c0:c1 + 1] - G["cs"][c0])
@@ -42,8 +39,7 @@ def test_shards_are_pieces_and_concatenate_bitwise(world, C, sigma):
         assert np.array_equal(F["col"], G["col"][G["cs"][c0]:G["cs"][c1]])
         if sigma > 1:
             assert np.array_equal(F["perm"] + r0, G["perm"][r0:r1])
-        ys = torch.empty(r1 - r0, dtype=torch.float64, device="cuda")
-        sell.sell_spmv(hs, x, ys)
+        ys = sdist.sharded_spmv(shard, x[r0:r1], gather=lambda xl: x)
         parts.append(ys)
         hs.free()
     torch.cuda.synchronize()
