@@ -368,10 +368,16 @@ typedef struct {
     int32_t size_ratio;   /* 0 or 1: a batch takes queued requests in arrival order; r > 1: a batch takes
                              the oldest request, then later ones whose work (stored elements x k) is
                              within a factor r of it, so small requests do not wait for a large one */
-    int32_t reserved;     /* 0 */
+    int32_t express_streams; /* 0, or this many of the `streams` (fewer than all) are express lanes:
+                                created with the highest stream priority and reserved for small
+                                requests (work at most express_work); the oldest small requests go
+                                there ahead of large ones, and batches on the other streams then hold
+                                one size class each */
     int64_t max_batch_work; /* 0: no cap; w > 0: with size_ratio <= 1, a batch stops taking requests
                                once its work (stored elements x k) would exceed w (it always takes
                                at least one) */
+    int64_t express_work;   /* > 0 exactly when express_streams > 0: the largest work (stored
+                               elements x k) of a small request */
 } sell_server_opts;
 
 typedef struct {
@@ -452,6 +458,18 @@ SELL_API sell_status sell_bench_read(const void *buf, size_t bytes, double *sink
  * model assumes infinitely fast caches).  Errors: SELL_EINVAL, SELL_ECUDA. */
 SELL_API sell_status sell_bench_gather(const void *x, int64_t n, double *sink, int32_t grid, int32_t iters,
                                        void *stream);
+
+/* The random-gather rate through the tensor memory accelerator instead of
+ * the load/store path: x (n words of 8 bytes, n even, 16-byte aligned) is
+ * viewed as n / 2 rows of 16 bytes, and every thread of grid x 128 issues
+ * `iters` tile::gather4 copies of four random rows each into shared memory
+ * (a linear congruential sequence, as sell_bench_gather).  Rows gathered per
+ * second = grid x 128 x iters x 4 / time; every row is one 32-byte sector
+ * fetch from L2.  sink holds grid x 128 + 1 doubles, the last one 0 on
+ * entry: it is set to 1 if a bounded wait for the copies gave up.  Errors:
+ * SELL_EINVAL, SELL_EUNSUPPORTED (no tensor-map encoder), SELL_ECUDA. */
+SELL_API sell_status sell_bench_gather4(const void *x, int64_t n, double *sink, int32_t grid, int32_t iters,
+                                        void *stream);
 
 /* Binary64 fused multiply-add throughput kernel: every thread of
  * grid x 256 threads runs `iters` x 64 dependent-chain FMAs on 8 independent

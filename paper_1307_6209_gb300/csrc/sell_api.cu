@@ -415,6 +415,11 @@ sell_status sell_bench_gather(const void *x, int64_t n, double *sink, int32_t gr
     return bench_gather(x, n, sink, grid, iters, static_cast<cudaStream_t>(stream));
 }
 
+sell_status sell_bench_gather4(const void *x, int64_t n, double *sink, int32_t grid, int32_t iters,
+                               void *stream) {
+    return bench_gather4(x, n, sink, grid, iters, static_cast<cudaStream_t>(stream));
+}
+
 sell_status sell_bench_fma64(double *sink, int32_t grid, int32_t iters, void *stream) {
     return bench_fma64(sink, grid, iters, static_cast<cudaStream_t>(stream));
 }

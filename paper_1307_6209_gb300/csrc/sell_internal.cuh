@@ -177,5 +177,6 @@ void batch_release(sell_batch *b, cudaStream_t s);
 sell_status bench_read(const void *buf, size_t bytes, double *sink, int32_t grid, cudaStream_t s);
 sell_status bench_fma64(double *sink, int32_t grid, int32_t iters, cudaStream_t s);
 sell_status bench_gather(const void *x, int64_t n, double *sink, int32_t grid, int32_t iters, cudaStream_t s);
+sell_status bench_gather4(const void *x, int64_t n, double *sink, int32_t grid, int32_t iters, cudaStream_t s);
 
 }  // namespace sell

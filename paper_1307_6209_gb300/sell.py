@@ -67,7 +67,8 @@ class sell_batch_item(ctypes.Structure):
 
 class sell_server_opts(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_int64), ("max_batch", ctypes.c_int32), ("streams", ctypes.c_int32),
-                ("size_ratio", ctypes.c_int32), ("reserved", ctypes.c_int32), ("max_batch_work", ctypes.c_int64)]
+                ("size_ratio", ctypes.c_int32), ("express_streams", ctypes.c_int32),
+                ("max_batch_work", ctypes.c_int64), ("express_work", ctypes.c_int64)]
 
 
 class sell_request_info(ctypes.Structure):
@@ -123,6 +124,7 @@ SIGNATURES = {
     "sell_bench_read": (ctypes.c_int, [_P, ctypes.c_size_t, _P, ctypes.c_int32, _P]),
     "sell_bench_fma64": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P]),
     "sell_bench_gather": (ctypes.c_int, [_P, ctypes.c_int64, _P, ctypes.c_int32, ctypes.c_int32, _P]),
+    "sell_bench_gather4": (ctypes.c_int, [_P, ctypes.c_int64, _P, ctypes.c_int32, ctypes.c_int32, _P]),
 }
 
 _lib = None
@@ -422,6 +424,10 @@ def sell_bench_gather(x, n: int, sink, grid: int, iters: int, stream=None):
     _check(load().sell_bench_gather(_ptr(x), int(n), _ptr(sink), int(grid), int(iters), _stream_ptr(stream)))
 
 
+def sell_bench_gather4(x, n: int, sink, grid: int, iters: int, stream=None):
+    _check(load().sell_bench_gather4(_ptr(x), int(n), _ptr(sink), int(grid), int(iters), _stream_ptr(stream)))
+
+
 def sell_bench_fma64(sink, grid: int, iters: int, stream=None):
     _check(load().sell_bench_fma64(_ptr(sink), int(grid), int(iters), _stream_ptr(stream)))
 
@@ -459,9 +465,10 @@ def use_torch_allocator(enable: bool = True):
 
 # ------------------------------------------------------------------ serving
 def sell_server_create(mats, budget_bytes: int, max_batch: int = 64, streams: int = 3, size_ratio: int = 0,
-                       max_batch_work: int = 0) -> int:
+                       max_batch_work: int = 0, express_streams: int = 0, express_work: int = 0) -> int:
     arr = (_P * len(mats))(*[m.handle.value for m in mats])
-    o = sell_server_opts(int(budget_bytes), int(max_batch), int(streams), int(size_ratio), 0, int(max_batch_work))
+    o = sell_server_opts(int(budget_bytes), int(max_batch), int(streams), int(size_ratio), int(express_streams),
+                         int(max_batch_work), int(express_work))
     out = _P()
     _check(load().sell_server_create(arr, len(mats), ctypes.byref(o), ctypes.byref(out)))
     return out.value

@@ -90,13 +90,15 @@ class Server:
     """Native server over resident matrices `mats` (list of SellMatrix)."""
 
     def __init__(self, mats, hbm_budget_bytes: int, max_batch: int = 128, streams: int = 6, size_ratio: int = 0,
-                 max_batch_work: int = 0):
+                 max_batch_work: int = 0, express_streams: int = 0, express_work: int = 0):
         self.mats = list(mats)
         self.resident = sum(h.info.device_bytes for h in self.mats)
         if self.resident >= hbm_budget_bytes:
             raise ValueError("resident matrices fill the HBM budget")
         self.budget = int(hbm_budget_bytes)
-        self.handle = sell.sell_server_create(self.mats, self.budget, max_batch, streams, size_ratio, max_batch_work)
+        self.express_work = int(express_work)
+        self.handle = sell.sell_server_create(self.mats, self.budget, max_batch, streams, size_ratio, max_batch_work,
+                                              express_streams, express_work)
         self._done = []
         self._done_lock = threading.Lock()
         self._pending = {}  # id -> Request, until collected
@@ -144,9 +146,13 @@ class Server:
         self._record(r)
         return r
 
+    def work(self, mid: int, k: int) -> int:
+        """A request's work as the server measures it: stored elements x k."""
+        return int(self.mats[mid].info.stored) * int(k)
+
     def _record(self, r: Request):
         with self._done_lock:
-            self._done.append((r.t_arrive, r.t_launch, r.t_done, r.batch))
+            self._done.append((r.t_arrive, r.t_launch, r.t_done, r.batch, self.work(r.mid, r.k)))
             self._pending.pop(r.rid, None)
 
     # ----------------------------------------------------------- lifecycle
@@ -165,16 +171,25 @@ class Server:
             pass
 
     # ----------------------------------------------------------- reporting
-    def stats(self):
+    def stats(self, split_work: int | None = None):
+        """Counters and latency percentiles; with a work threshold (the
+        server's express_work by default), also per size class: "small"
+        (work <= threshold) and "large"."""
         st = sell.sell_server_stats(self.handle) if self.handle else {}
         with self._done_lock:
-            d = np.array(self._done) if self._done else np.zeros((1, 4))
+            d = np.array(self._done, dtype=np.float64) if self._done else np.zeros((1, 5))
         lat = d[:, 2] - d[:, 0]
         out = {"requests": int(st.get("requests", len(self._done))), "batches": int(st.get("batches", 0)),
                "mean_batch": float(st["batched_requests"] / max(1, st["batches"])) if st else 0.0,
                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
                "mean_ms": float(lat.mean() * 1e3), "peak_hbm_bytes": int(st.get("peak_bytes", 0)),
                "budget_bytes": self.budget}
+        split = self.express_work if split_work is None else int(split_work)
+        if split > 0 and self._done:
+            for name, sel in (("small", d[:, 4] <= split), ("large", d[:, 4] > split)):
+                if sel.any():
+                    out[name] = {"requests": int(sel.sum()), "p50_ms": float(np.percentile(lat[sel], 50) * 1e3),
+                                 "p99_ms": float(np.percentile(lat[sel], 99) * 1e3)}
         return out
 
 

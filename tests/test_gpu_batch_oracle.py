@@ -185,3 +185,41 @@ def test_batch_benchmark_set(k):
     plan.free()
     for h in hs:
         h.free()
+
+
+def test_batch_tuning_knobs_keep_the_bits():
+    """The autotuner's knobs of a batch -- the right-hand-side block width of
+    each item (SELL_SPMV_RHS_BLOCK4/2/1) and the plan's block size (64, 128,
+    256 rows per work unit) -- change no bit of any product."""
+    import torch
+    from paper_1307_6209_gb300 import sell
+
+    rng = np.random.default_rng(14)
+    prods = []
+    for i in range(12):
+        N = int(rng.integers(300, 5000))
+        A = synth.lognormal(N, seed=400 + i, cap=900) if i % 2 else synth.banded(N, seed=400 + i)
+        store = [sell.SELL_F64, sell.SELL_F32, sell.SELL_BF16][i % 3]
+        prods.append(_product(A, store, [8, 5, 16][i % 3], 0, seed=500 + i, C=32, sigma=[1, 256][i % 2]))
+    plan = sell.sell_batch_create([(h, X, Y, fl) for h, A, X, Y, Y0, fl in prods])
+    plan.run()
+    torch.cuda.synchronize()
+    ref = [Y.clone() for _, _, _, Y, _, _ in prods]
+    _check(prods, "default")
+    plan.free()
+    for rhs in (sell.SELL_SPMV_RHS_BLOCK4, sell.SELL_SPMV_RHS_BLOCK2, sell.SELL_SPMV_RHS_BLOCK1):
+        for block in (64, 128, 256):
+            for _, _, _, Y, _, _ in prods:
+                Y.fill_(float("nan"))
+            plan = sell.sell_batch_create([(h, X, Y, fl | rhs) for h, A, X, Y, Y0, fl in prods])
+            plan.set_launch(block)
+            plan.run()
+            torch.cuda.synchronize()
+            for (h, A, X, Y, Y0, fl), r in zip(prods, ref):
+                assert torch.equal(Y, r), f"rhs flag {rhs:#x}, block {block}"
+            plan.free()
+    plan = sell.sell_batch_create([(h, X, Y, fl) for h, A, X, Y, Y0, fl in prods])
+    with pytest.raises(sell.SellError) as e:
+        plan.set_launch(96)
+    assert e.value.status == sell.SELL_EINVAL
+    plan.free()

@@ -284,3 +284,23 @@ def test_spmv_in_cuda_graph():
         g.replay()
         torch.cuda.synchronize()
         assert y.cpu().numpy().tobytes() == y_eager.cpu().numpy().tobytes()
+
+
+@pytest.mark.parametrize("k", [3, 8, 13])
+def test_spmmv_rhs_block_flags_keep_the_bits(k):
+    """SELL_SPMV_RHS_BLOCK4/2/1 only narrow the kernel's blocks of
+    right-hand sides: the result is the same bits as the default split."""
+    import torch
+    from paper_1307_6209_gb300 import sell
+
+    A = synth.lognormal(9000, seed=40 + k, cap=1500)
+    h = sell.sell_build(A, C=64, sigma=512)
+    X = torch.from_numpy(synth.block(A.ncols, k, seed=k)).cuda()
+    ref = torch.empty((A.nrows, k), dtype=torch.float64, device="cuda")
+    sell.sell_spmmv(h, X, ref)
+    for fl in (sell.SELL_SPMV_RHS_BLOCK4, sell.SELL_SPMV_RHS_BLOCK2, sell.SELL_SPMV_RHS_BLOCK1,
+               sell.SELL_SPMV_RHS_BLOCK4 | sell.SELL_SPMV_RHS_BLOCK1):
+        Y = torch.full((A.nrows, k), float("nan"), dtype=torch.float64, device="cuda")
+        sell.sell_spmmv(h, X, Y, flags=fl)
+        torch.cuda.synchronize()
+        assert torch.equal(Y, ref), f"flags {fl:#x}"
