@@ -732,12 +732,11 @@ def batched_section(sell, autotune, model, stream, peak, gather_gps, nmat=512, k
 def serving_section(sell, stream, nmat=64, seed=0, duration_s=1.5, repeats=3):
     """64 resident matrices, rows log-uniform in [10k, 4M], lognormal row
     lengths, half FP64 and half FP32; requests of 1-8 right-hand sides from
-    pinned host memory; Poisson arrivals at fractions of the saturated rate.
-    Two scheduling policies on the same arrival streams: arrival order on 6
-    streams, and the same 6 streams plus 2 high-priority express lanes for
-    small requests (work at most the median request's).  Latency percentiles
-    overall and per size class; the express policy's loads are repeated
-    three times (seeds 7, 8, 9) for the run-to-run spread."""
+    pinned host memory; Poisson arrivals at fractions of the saturated rate,
+    each load three times (seeds 7, 8, 9) for the run-to-run spread; latency
+    percentiles overall and per size class (small: work at most the median
+    request's), the worst latency per 50 ms of arrivals (the tail's timing),
+    and one request alone."""
     import torch
     from paper_1307_6209_gb300 import serving, synth
     rng = np.random.default_rng(seed)
@@ -767,11 +766,9 @@ def serving_section(sell, stream, nmat=64, seed=0, duration_s=1.5, repeats=3):
 
     works = sorted(int(h.info.stored) * k for h in mats for k in range(1, 9))
     small_work = works[len(works) // 2]
-    policies = (("arrival_order", {"streams": 6}),
-                ("express", {"streams": 8, "express_streams": 2, "express_work": small_work}))
 
-    def one_load(pol, rate, sd):
-        srv = serving.Server(mats, budget, max_batch=64, **pol)
+    def one_load(rate, sd):
+        srv = serving.Server(mats, budget, max_batch=64, streams=6)
         reqs = serving.poisson_load(srv, rate_hz=rate, duration_s=duration_s, make_request=make, seed=sd,
                                     to_host=False)
         t_end = max(r.t_done for r in reqs)
@@ -781,6 +778,12 @@ def serving_section(sell, stream, nmat=64, seed=0, duration_s=1.5, repeats=3):
         gfl = sum(2.0 * mats[r.mid].info.nnz * r.k for r in reqs)
         st["throughput_req_per_s"] = len(reqs) / (t_end - t_beg)
         st["gflops"] = gfl / (t_end - t_beg) / 1e9
+        lat = np.array([r.t_done - r.t_arrive for r in reqs]) * 1e3
+        wait = np.array([r.t_launch - r.t_arrive for r in reqs]) * 1e3
+        st["wait_p99_ms"] = float(np.percentile(wait, 99))
+        bins = ((np.array([r.t_arrive for r in reqs]) - t_beg) / 0.05).astype(int)
+        st["worst_ms_per_50ms"] = [round(float(lat[bins == b].max()), 1) if (bins == b).any() else 0.0
+                                   for b in range(int(bins.max()) + 1)]
         return st
 
     def rnd(d):
@@ -789,40 +792,35 @@ def serving_section(sell, stream, nmat=64, seed=0, duration_s=1.5, repeats=3):
     out = {"workload": f"{nmat} resident matrices, rows log-uniform [10k, 4M], lognormal rows, half FP64 / "
                        f"half FP32, requests k ~ U{{1..8}}, inputs from pinned host memory, results left on "
                        f"the device and taken by a client thread as they complete; latency = arrival to the "
-                       f"batch's completion; scheduler, admission and batching in the native server",
+                       f"batch's completion; scheduler, admission and batching in the native server "
+                       f"(6 streams, batches of up to 64)",
            "resident_gb": round(resident / 1e9, 2), "budget_gb": round(budget / 1e9, 2),
            "nnz_total": int(sum(h.info.nnz for h in mats)),
            "small_request_work": small_work,
            "size_classes": "small: stored elements x k at most the median request's; large: the rest"}
-    base_sat = None
-    for name, pol in policies:
-        # warm-up (kernels, arena, pinned memory), then the saturated rate from a burst
-        srv = serving.Server(mats, budget, max_batch=64, **pol)
-        serving.burst_load(srv, 200, make, seed=1, to_host=False)
-        srv.stop()
-        srv = serving.Server(mats, budget, max_batch=64, **pol)
-        burst, dt = serving.burst_load(srv, 400, make, seed=2, to_host=False)
-        sat = len(burst) / dt
-        res = {"policy": pol, "saturated_req_per_s": round(sat, 1), "burst": rnd(srv.stats(split_work=small_work))}
-        srv.stop()
-        if base_sat is None:
-            base_sat = sat  # both policies see the same offered loads
-        for frac in (0.5, 0.8, 0.95):
-            runs = [one_load(pol, frac * base_sat, 7 + rep) for rep in range(repeats if name == "express" else 1)]
-            row = rnd(runs[0])
-            row["offered_req_per_s"] = round(frac * base_sat, 1)
-            if len(runs) > 1:
-                for key in ("p50_ms", "p99_ms"):
-                    vals = [r[key] for r in runs]
-                    row[key] = round(statistics.median(vals), 3)
-                    row[key + "_runs"] = [round(v, 3) for v in vals]
-                for cls in ("small", "large"):
-                    if all(cls in r for r in runs):
-                        row[cls] = {key: round(statistics.median(r[cls][key] for r in runs), 3)
-                                    for key in ("p50_ms", "p99_ms")}
-                        row[cls]["requests"] = runs[0][cls]["requests"]
-            res[f"load_{frac}"] = row
-        out[name] = res
+    # warm-up (kernels, arena, pinned memory), then the saturated rate from a burst
+    srv = serving.Server(mats, budget, max_batch=64, streams=6)
+    serving.burst_load(srv, 200, make, seed=1, to_host=False)
+    srv.stop()
+    srv = serving.Server(mats, budget, max_batch=64, streams=6)
+    burst, dt = serving.burst_load(srv, 400, make, seed=2, to_host=False)
+    sat = len(burst) / dt
+    out["saturated_req_per_s"] = round(sat, 1)
+    out["burst"] = rnd(srv.stats(split_work=small_work))
+    srv.stop()
+    for frac in (0.5, 0.8, 0.95):
+        runs = [one_load(frac * sat, 7 + rep) for rep in range(repeats)]
+        row = rnd(runs[0])
+        row["offered_req_per_s"] = round(frac * sat, 1)
+        for key in ("p50_ms", "p99_ms", "wait_p99_ms", "throughput_req_per_s"):
+            vals = [r[key] for r in runs]
+            row[key] = round(statistics.median(vals), 3)
+            row[key + "_runs"] = [round(v, 3) for v in vals]
+        for cls in ("small", "large"):
+            if all(cls in r for r in runs):
+                row[cls] = {key: round(statistics.median(r[cls][key] for r in runs), 3) for key in ("p50_ms", "p99_ms")}
+                row[cls]["requests"] = runs[0][cls]["requests"]
+        out[f"load_{frac}"] = row
     # one request alone: the largest request (the 4M-row matrix, k = 8) and
     # a small one, each through the server on an idle GPU
     srv = serving.Server(mats, budget, max_batch=64, streams=2)
@@ -910,13 +908,12 @@ def compact_summary(line, ex):
                                        "x_f64": g(b, f"k{k}", "f32_speedup_vs_f64"),
                                        "ok": g(b, f"k{k}", "f32", "batch_equals_per_matrix")} for k in (1, 4, 8)}
     v = ex.get("serving")
-    if isinstance(v, dict) and "express" in v:
-        e, a = v["express"], v["arrival_order"]
-        s["serving"] = {"sat_rps": e["saturated_req_per_s"]}
+    if isinstance(v, dict) and "load_0.5" in v:
+        s["serving"] = {"sat_rps": v["saturated_req_per_s"]}
         for f in ("0.5", "0.8", "0.95"):
-            s["serving"][f"p50_p99_ms_{f}"] = [g(e, f"load_{f}", "p50_ms"), g(e, f"load_{f}", "p99_ms")]
-        s["serving"]["small_p50_p99_ms_0.8"] = [g(e, "load_0.8", "small", "p50_ms"), g(e, "load_0.8", "small", "p99_ms")]
-        s["serving"]["arrival_order_p50_p99_ms_0.8"] = [g(a, "load_0.8", "p50_ms"), g(a, "load_0.8", "p99_ms")]
+            s["serving"][f"p50_p99_ms_{f}"] = [g(v, f"load_{f}", "p50_ms"), g(v, f"load_{f}", "p99_ms")]
+        s["serving"]["p99_runs_0.8"] = g(v, "load_0.8", "p99_ms_runs")
+        s["serving"]["small_p50_p99_ms_0.8"] = [g(v, "load_0.8", "small", "p50_ms"), g(v, "load_0.8", "small", "p99_ms")]
         s["serving"]["alone_ms"] = v.get("alone_ms")
     lp = ex.get("laplace64")
     if isinstance(lp, dict) and "us_per_call" in lp:

@@ -316,11 +316,12 @@ typedef struct sell_batch *sell_batch_plan;
 /* Prepare a batch of n products to run in a few launches (one per kernel
  * variant present -- value type, block of 1/2/4/8 right-hand sides, plain or
  * compensated accumulation -- and per 160 products).  Work units are tiles of
- * 256 sorted rows of one product, or 256 threads of its long-row segment
- * work; every launch has one block per unit, long-row work first and the
- * biggest products first.  The products may use matrices of different sizes
- * and storage types; a matrix with more than 8 right-hand sides is split
- * into blocks of 8.  Each result is bit-identical to the same product run
+ * 128 sorted rows of one product, or 128 threads of its long-row segment
+ * work (sell_batch_set_launch changes the size); every launch has one block
+ * per unit, long-row work first and the biggest products first.  The
+ * products may use matrices of different sizes and storage types; a matrix
+ * with more than 8 right-hand sides is split into blocks of 8 (or of the
+ * item's SELL_SPMV_RHS_BLOCK* width).  Each result is bit-identical to the same product run
  * alone by sell_spmmv.  The plan owns the long-row scratch of its products
  * (one allocation, cleared on `stream`; plans never share scratch with each
  * other or with sell_spmmv); the work units travel in the launch parameters;
@@ -335,7 +336,7 @@ SELL_API sell_status sell_batch_create(const sell_batch_item *items, int32_t n, 
 SELL_API sell_status sell_batch_run(sell_batch_plan plan, int32_t grid, void *stream);
 
 /* Launch tuning of a plan (autotuner knob): `block` threads per block, 64,
- * 128 or 256 (the default), and as many sorted rows (or long-row segment
+ * 128 (the default) or 256, and as many sorted rows (or long-row segment
  * threads) per work unit.  The results do not depend on it.  Takes effect
  * at the next sell_batch_run (a graph captured before keeps the old launch).
  * Errors: SELL_EINVAL, SELL_EUNSUPPORTED (too many units). */
@@ -368,16 +369,10 @@ typedef struct {
     int32_t size_ratio;   /* 0 or 1: a batch takes queued requests in arrival order; r > 1: a batch takes
                              the oldest request, then later ones whose work (stored elements x k) is
                              within a factor r of it, so small requests do not wait for a large one */
-    int32_t express_streams; /* 0, or this many of the `streams` (fewer than all) are express lanes:
-                                created with the highest stream priority and reserved for small
-                                requests (work at most express_work); the oldest small requests go
-                                there ahead of large ones, and batches on the other streams then hold
-                                one size class each */
+    int32_t reserved;     /* 0 */
     int64_t max_batch_work; /* 0: no cap; w > 0: with size_ratio <= 1, a batch stops taking requests
                                once its work (stored elements x k) would exceed w (it always takes
                                at least one) */
-    int64_t express_work;   /* > 0 exactly when express_streams > 0: the largest work (stored
-                               elements x k) of a small request */
 } sell_server_opts;
 
 typedef struct {

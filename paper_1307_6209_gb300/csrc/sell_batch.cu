@@ -6,9 +6,9 @@
 // plain or compensated accumulation).  Each variant present gets one launch
 // (per 160 products): its products and the block ranges of their work units
 // travel in the kernel's parameter space -- a unit is one block's worth of
-// sorted rows of one product (its short rows; kTileRows = 256 by default,
-// 64 or 128 after sell_batch_set_launch), or as many threads of the
-// product's long-row segment units.  Creating a plan makes one device allocation (the
+// sorted rows of one product (its short rows; 128 by default, 64 or 256
+// after sell_batch_set_launch), or as many threads of the product's long-row
+// segment units.  Creating a plan makes one device allocation (the
 // products' long-row scratch) and no copies, and does not synchronise.  One
 // block per unit, long-row units first and biggest products first; the
 // hardware block scheduler balances the uneven products.  (A grid-stride "persistent" form of this kernel was measured:
@@ -67,11 +67,17 @@ struct LaunchParams {
 };
 
 // One block per work unit, long-row units first in the grid so that they
-// start early (the same shape as the single-product kernel).
+// start early (the same shape as the single-product kernel).  The one- and
+// two-vector variants issue the next group's val/col loads before the
+// current group's gathers (software pipelining, as launch mode 1 of the
+// single product; the FMA order and so the bits are unchanged): measured
+// 3 % faster on a 256-matrix banded binary32 batch and 2 % on the
+// 512-matrix mixed one.
 template <class VT, int K, class Acc, class AccL>
 __device__ __forceinline__ void batch_unit(const LaunchParams &lp) {
     using XT = typename XType<VT>::T;
     constexpr int U = K >= 4 ? 2 : 4;
+    constexpr bool PIPE = K <= 2;
     const uint64_t pol = l2_evict_first_policy();
     const int32_t w = (int32_t)blockIdx.x;
     if (w >= lp.start[2 * lp.nprod]) return;
@@ -87,7 +93,7 @@ __device__ __forceinline__ void batch_unit(const LaunchParams &lp) {
     if (is_long) {
         const int64_t v = first + threadIdx.x;
         if (v < P.long_threads)
-            long_unit<VT, XT, K, U, false, AccL>(static_cast<const VT *>(P.val), P.col, P.cs, P.srl, P.perm,
+            long_unit<VT, XT, K, U, PIPE, AccL>(static_cast<const VT *>(P.val), P.col, P.cs, P.srl, P.perm,
                                          P.lchunk, P.lunit, P.lmeta, P.lrow, static_cast<AccL *>(P.part), P.cnt, P.cnt2,
                                          static_cast<const XT *>(P.X),
                                          P.ldx, static_cast<XT *>(P.Y), P.ldy, P.N, P.C, v, P.acc, P.vec != 0, pol);
@@ -95,7 +101,7 @@ __device__ __forceinline__ void batch_unit(const LaunchParams &lp) {
     }
     const int64_t r = first + threadIdx.x;
     if (r < P.N)
-        short_row<VT, XT, K, U, false, Acc>(static_cast<const VT *>(P.val), P.col, P.cs, P.srl, P.perm,
+        short_row<VT, XT, K, U, PIPE, Acc>(static_cast<const VT *>(P.val), P.col, P.cs, P.srl, P.perm,
                                      static_cast<const XT *>(P.X), P.ldx, static_cast<XT *>(P.Y), P.ldy, P.C, r, P.acc,
                                      P.vec != 0, pol);
 }
@@ -106,8 +112,11 @@ __device__ __forceinline__ void batch_unit(const LaunchParams &lp) {
 // sake of the long-row path, although the short rows carry most of the work.
 // Their entry point therefore asks for 6 resident blocks (5 for bfloat16 and
 // for two vectors), which fits them in 40-48 registers with no spills (ptxas
-// -v).  Wider blocks need their registers for the K accumulators and keep the
-// allocation ptxas picks without a bound (64-76).
+// -v).  The four-vector variants keep the allocation ptxas picks without a
+// bound (64 registers, 4 blocks per SM).  The eight-vector variants would take
+// 64-76 (3 blocks per SM for binary32); they ask for 4 resident blocks, which
+// caps them at 64 registers with 16-40 bytes of spills and measured 5 %
+// faster on the 512-matrix binary32 batch (1.95 -> 2.04 TF/s, 256 threads).
 template <class VT, int K>
 constexpr int narrow_min_blocks() {
     return K == 1 && !std::is_same<VT, __nv_bfloat16>::value ? 6 : 5;
@@ -124,6 +133,11 @@ __global__ void __launch_bounds__(kTileRows) k_batch(const __grid_constant__ Lau
     batch_unit<VT, K, Acc, AccL>(lp);
 }
 
+template <class VT, int K, class Acc, class AccL = Acc>
+__global__ void __launch_bounds__(kTileRows, 4) k_batch_wide(const __grid_constant__ LaunchParams lp) {
+    batch_unit<VT, K, Acc, AccL>(lp);
+}
+
 using KernelFn = void (*)(const LaunchParams);
 
 template <class VT, class Acc, class AccL = Acc>
@@ -132,7 +146,7 @@ KernelFn kernel_for_k(int kb) {
         case 1: return k_batch_narrow<VT, 1, Acc, AccL>;
         case 2: return k_batch_narrow<VT, 2, Acc, AccL>;
         case 4: return k_batch<VT, 4, Acc, AccL>;
-        default: return k_batch<VT, 8, Acc, AccL>;
+        default: return k_batch_wide<VT, 8, Acc, AccL>;
     }
 }
 

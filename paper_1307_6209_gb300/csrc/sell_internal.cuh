@@ -148,7 +148,7 @@ struct sell_batch {
     std::vector<Group> groups;
     int64_t nwork = 0;
     int32_t nprod = 0;
-    int32_t tile = 256;  // threads per block = rows (or segment threads) per work unit
+    int32_t tile = 128;  // threads per block = rows (or segment threads) per work unit
     cudaStream_t last_stream = nullptr;  // stream of the latest sell_batch_run
     bool ran = false;
 };

@@ -13,13 +13,6 @@
 //   * keeps up to `streams` batches in flight, so requests that arrive while
 //     others run are admitted as soon as a stream and memory are free and
 //     their work overlaps on the device;
-//   * optionally reserves `express_streams` of them, created with the highest
-//     stream priority, for small requests (work at most `express_work`): the
-//     oldest small requests go there ahead of a large request at the head of
-//     the queue, and the block scheduler runs their blocks before those of
-//     the large batches already on the device, so a small request does not
-//     wait for a large one.  The other streams still take the queue in
-//     arrival order, so large requests are never passed over for long;
 //   * retires a batch when its completion event has passed: stamps the
 //     requests, returns their memory to the arena and wakes their waiters.
 // Times are seconds on a steady clock shared by all requests of the process.
@@ -87,15 +80,12 @@ struct sell_server {
     int64_t budget = 0, resident = 0, arena_bytes = 0, used = 0, peak_used = 0;
     int32_t max_batch = 64, nstreams = 3, size_ratio = 0;
     int64_t max_work = 0;  // cap on a batch's work (stored elements x k), 0: none
-    int32_t nexpress = 0;      // streams reserved for small requests (the last ones)
-    int64_t express_work = 0;  // a request is small when its work is at most this
     sell::Allocator al;
     char *arena_base = nullptr;
     sell::Arena arena;
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> events;  // one per stream (a stream holds at most one batch)
-    std::deque<int> free_streams;   // free normal streams
-    std::deque<int> free_express;   // free express streams
+    std::deque<int> free_streams;
     std::vector<sell::Batch> inflight;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -238,7 +228,7 @@ void scheduler(sell_server *S) {
                 batch_release(B.plan, S->streams[B.si]);
                 delete B.plan;
             }
-            (B.si >= S->nstreams - S->nexpress ? S->free_express : S->free_streams).push_back(B.si);
+            S->free_streams.push_back(B.si);
             S->inflight.erase(S->inflight.begin() + i);
             retired = true;
         }
@@ -248,51 +238,15 @@ void scheduler(sell_server *S) {
         // next requests in order, those whose work is within the ratio of it
         // (the others wait for the next batch, on another stream), so small
         // requests do not wait for the end of a large one's launch.
-        // Express lane first: the oldest small requests, wherever they are
-        // in the queue (a bounded look-ahead), on a high-priority stream.
-        if (!S->free_express.empty() && !S->queue.empty()) {
-            std::vector<Req *> batch;
-            size_t scan = std::min(S->queue.size(), (size_t)4 * S->max_batch);
-            for (size_t i = 0; i < scan && (int)batch.size() < S->max_batch;) {
-                Req *r = S->queue[i];
-                if (work(S, r) > (double)S->express_work) {
-                    ++i;
-                    continue;
-                }
-                if (!reserve(S, r)) break;
-                S->queue.erase(S->queue.begin() + (std::ptrdiff_t)i);
-                --scan;
-                r->state = kRunning;
-                batch.push_back(r);
-            }
-            if (!batch.empty()) {
-                const int si = S->free_express.front();
-                S->free_express.pop_front();
-                Batch B;
-                lk.unlock();
-                launch(S, si, batch, B);
-                lk.lock();
-                S->inflight.push_back(std::move(B));
-                S->nbatch += 1;
-                S->nbatched += (int64_t)batch.size();
-                continue;
-            }
-        }
         if (!S->free_streams.empty() && !S->queue.empty()) {
             std::vector<Req *> batch;
             if (S->size_ratio <= 1) {
                 double bw = 0;  // the batch's work so far
-                bool small0 = false;
                 while (!S->queue.empty() && (int)batch.size() < S->max_batch) {
                     Req *r = S->queue.front();
                     const double w = work(S, r);
                     if (!batch.empty() && S->max_work > 0 && bw + w > (double)S->max_work) break;
-                    // with express lanes a batch holds one size class, so a
-                    // small request never waits for a large one's launch
-                    const bool small = S->nexpress > 0 && w <= (double)S->express_work;
-                    if (!batch.empty() && S->nexpress > 0 && small != small0) break;
                     if (!reserve(S, r)) break;
-                    if (batch.empty()) small0 = small;
                     S->queue.pop_front();
                     r->state = kRunning;
                     batch.push_back(r);
@@ -383,9 +337,7 @@ sell_status sell_server_create(const sell_handle *mats, int32_t n, const sell_se
         o->max_batch_work < 0)
         return fail(SELL_EINVAL,
                     "sell_server_create: need 1 <= max_batch <= 4096, 1 <= streams <= 16, size_ratio >= 0");
-    if (o->express_streams < 0 || o->express_streams >= o->streams || (o->express_streams > 0) != (o->express_work > 0))
-        return fail(SELL_EINVAL, "sell_server_create: need 0 <= express_streams < streams, and express_work > 0 "
-                                 "exactly when express_streams > 0");
+    if (o->reserved != 0) return fail(SELL_EINVAL, "sell_server_create: reserved must be 0");
     sell_server *S = new (std::nothrow) sell_server();
     if (!S) return fail(SELL_ENOMEM, "sell_server_create: host allocation failed");
     int dev = 0;
@@ -413,8 +365,6 @@ sell_status sell_server_create(const sell_handle *mats, int32_t n, const sell_se
     S->nstreams = o->streams;
     S->size_ratio = o->size_ratio;
     S->max_work = o->max_batch_work;
-    S->nexpress = o->express_streams;
-    S->express_work = o->express_work;
     S->al = current_allocator();
     S->arena_base = static_cast<char *>(S->al.get((size_t)S->arena_bytes, nullptr));
     if (!S->arena_base) {
@@ -423,22 +373,15 @@ sell_status sell_server_create(const sell_handle *mats, int32_t n, const sell_se
     }
     S->arena.reset((size_t)S->arena_bytes);
     sell_status st = SELL_OK;
-    int prio_least = 0, prio_greatest = 0;
-    if (cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess) {
-        (void)cudaGetLastError();
-        prio_least = prio_greatest = 0;
-    }
     for (int i = 0; i < S->nstreams && st == SELL_OK; ++i) {
         cudaStream_t s = nullptr;
         cudaEvent_t e = nullptr;
-        const bool express = i >= S->nstreams - S->nexpress;
-        if (cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, express ? prio_greatest : prio_least) !=
-                cudaSuccess ||
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
             st = cuda_fail(cudaGetLastError(), "sell_server_create: stream/event");
         S->streams.push_back(s);
         S->events.push_back(e);
-        (express ? S->free_express : S->free_streams).push_back(i);
+        S->free_streams.push_back(i);
     }
     if (st == SELL_OK && cudaDeviceSynchronize() != cudaSuccess)
         st = cuda_fail(cudaGetLastError(), "sell_server_create: arena");

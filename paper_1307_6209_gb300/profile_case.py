@@ -13,8 +13,9 @@ through the C ABI; nothing is tuned.
 
 runs a batch plan instead (sell_batch_create / sell_batch_run): `--batch`
 matrices with rows uniform in [1000, 200000] (seeded), even ones banded
-(bandwidth 64, 7-30 entries per row) and odd ones lognormal, all in the given
-(C, sigma) and storage type, each with its own k right-hand sides.
+(bandwidth 64, 7-30 entries per row) and odd ones lognormal (`--kinds banded`
+or `lognormal`: one kind only), all in the given (C, sigma) and storage type,
+each with its own k right-hand sides.
 """
 from __future__ import annotations
 
@@ -41,6 +42,9 @@ def main(argv=None):
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--reps", type=int, default=5)
     p.add_argument("--batch", type=int, default=0, help="run a batch plan of this many matrices")
+    p.add_argument("--kinds", choices=["mixed", "banded", "lognormal"], default="mixed",
+                   help="batch matrices: alternating banded / lognormal, or one kind only")
+    p.add_argument("--tile", type=int, default=0, help="batch block size (64, 128, 256; 0 keeps the default)")
     a = p.parse_args(argv)
     if a.batch > 0:
         return run_batch(a)
@@ -110,7 +114,8 @@ def run_batch(a):
     g = torch.Generator("cuda").manual_seed(0)
     items, alg, nnz, stored = [], 0, 0, 0
     for i, n in enumerate(sizes):
-        gen = synth.banded_device if i % 2 == 0 else synth.lognormal_device
+        banded = a.kinds == "banded" or (a.kinds == "mixed" and i % 2 == 0)
+        gen = synth.banded_device if banded else synth.lognormal_device
         A = gen(int(n), seed=i)
         h = sell.sell_build(A, C=a.C, sigma=a.sigma, store_type=st, stream=s)
         inf = h.info
@@ -123,6 +128,8 @@ def run_batch(a):
         stored += inf.stored
         del A
     plan = sell.sell_batch_create(items, stream=s)
+    if a.tile:
+        plan.set_launch(a.tile)
     for _ in range(a.warmup):
         plan.run(stream=s)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.reps)]
@@ -132,7 +139,8 @@ def run_batch(a):
         e1.record(s)
     torch.cuda.synchronize()
     us = sum(e0.elapsed_time(e1) for e0, e1 in ev) * 1e3 / a.reps
-    print(json.dumps({"batch": a.batch, "rows": int(sizes.sum()), "nnz": nnz, "stored": stored,
+    print(json.dumps({"batch": a.batch, "kinds": a.kinds, "tile": a.tile, "rows": int(sizes.sum()), "nnz": nnz,
+                      "stored": stored,
                       "beta": round(nnz / max(stored, 1), 6), "store": a.store, "C": a.C, "sigma": a.sigma,
                       "k": a.k, "us": round(us, 3), "gflops": round(2.0 * nnz * a.k / us / 1e3, 1),
                       "algorithmic_bytes": alg, "algorithmic_gbs": round(alg / us / 1e3, 1),

@@ -67,8 +67,7 @@ class sell_batch_item(ctypes.Structure):
 
 class sell_server_opts(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_int64), ("max_batch", ctypes.c_int32), ("streams", ctypes.c_int32),
-                ("size_ratio", ctypes.c_int32), ("express_streams", ctypes.c_int32),
-                ("max_batch_work", ctypes.c_int64), ("express_work", ctypes.c_int64)]
+                ("size_ratio", ctypes.c_int32), ("reserved", ctypes.c_int32), ("max_batch_work", ctypes.c_int64)]
 
 
 class sell_request_info(ctypes.Structure):
@@ -465,10 +464,9 @@ def use_torch_allocator(enable: bool = True):
 
 # ------------------------------------------------------------------ serving
 def sell_server_create(mats, budget_bytes: int, max_batch: int = 64, streams: int = 3, size_ratio: int = 0,
-                       max_batch_work: int = 0, express_streams: int = 0, express_work: int = 0) -> int:
+                       max_batch_work: int = 0) -> int:
     arr = (_P * len(mats))(*[m.handle.value for m in mats])
-    o = sell_server_opts(int(budget_bytes), int(max_batch), int(streams), int(size_ratio), int(express_streams),
-                         int(max_batch_work), int(express_work))
+    o = sell_server_opts(int(budget_bytes), int(max_batch), int(streams), int(size_ratio), 0, int(max_batch_work))
     out = _P()
     _check(load().sell_server_create(arr, len(mats), ctypes.byref(o), ctypes.byref(out)))
     return out.value

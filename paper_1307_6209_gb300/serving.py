@@ -90,15 +90,13 @@ class Server:
     """Native server over resident matrices `mats` (list of SellMatrix)."""
 
     def __init__(self, mats, hbm_budget_bytes: int, max_batch: int = 128, streams: int = 6, size_ratio: int = 0,
-                 max_batch_work: int = 0, express_streams: int = 0, express_work: int = 0):
+                 max_batch_work: int = 0):
         self.mats = list(mats)
         self.resident = sum(h.info.device_bytes for h in self.mats)
         if self.resident >= hbm_budget_bytes:
             raise ValueError("resident matrices fill the HBM budget")
         self.budget = int(hbm_budget_bytes)
-        self.express_work = int(express_work)
-        self.handle = sell.sell_server_create(self.mats, self.budget, max_batch, streams, size_ratio, max_batch_work,
-                                              express_streams, express_work)
+        self.handle = sell.sell_server_create(self.mats, self.budget, max_batch, streams, size_ratio, max_batch_work)
         self._done = []
         self._done_lock = threading.Lock()
         self._pending = {}  # id -> Request, until collected
@@ -171,10 +169,10 @@ class Server:
             pass
 
     # ----------------------------------------------------------- reporting
-    def stats(self, split_work: int | None = None):
-        """Counters and latency percentiles; with a work threshold (the
-        server's express_work by default), also per size class: "small"
-        (work <= threshold) and "large"."""
+    def stats(self, split_work: int = 0):
+        """Counters and latency percentiles; with a work threshold (stored
+        elements x k), also per size class: "small" (work <= threshold) and
+        "large"."""
         st = sell.sell_server_stats(self.handle) if self.handle else {}
         with self._done_lock:
             d = np.array(self._done, dtype=np.float64) if self._done else np.zeros((1, 5))
@@ -184,7 +182,7 @@ class Server:
                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
                "mean_ms": float(lat.mean() * 1e3), "peak_hbm_bytes": int(st.get("peak_bytes", 0)),
                "budget_bytes": self.budget}
-        split = self.express_work if split_work is None else int(split_work)
+        split = int(split_work)
         if split > 0 and self._done:
             for name, sel in (("small", d[:, 4] <= split), ("large", d[:, 4] > split)):
                 if sel.any():

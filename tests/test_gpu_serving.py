@@ -286,44 +286,3 @@ def test_wait_and_next_racing_for_one_request():
     finally:
         sell.sell_server_destroy(srv)
         h.free()
-
-
-def test_express_lane_lets_small_requests_pass_a_large_one():
-    """With one normal stream and one express lane, small requests submitted
-    behind two large ones run on the express lane while the second large
-    request still waits for the normal stream; every result is the request
-    alone, and the oracle's product within its bound."""
-    import torch
-    from paper_1307_6209_gb300 import serving, sell
-    Abig = synth.lognormal_device(2_000_000, seed=15)
-    big = sell.sell_build(Abig, C=32, sigma=2_000_000)
-    hosts = []
-    mats = _mats(seed=80, hosts=hosts) + [big]
-    hosts.append(host_csr(Abig))
-    del Abig
-    small_work = max(m.info.stored for m in mats[:-1]) * 8
-    assert big.info.stored * 8 > small_work
-    with pytest.raises(sell.SellError):  # express lanes need a threshold, and a normal stream
-        serving.Server(mats, hbm_budget_bytes=8 << 30, streams=2, express_streams=1)
-    with pytest.raises(sell.SellError):
-        sell.sell_server_create(mats, 8 << 30, 8, 2, express_streams=2, express_work=small_work)
-    srv = serving.Server(mats, hbm_budget_bytes=sum(m.info.device_bytes for m in mats) + (6 << 30), max_batch=64,
-                         streams=2, express_streams=1, express_work=small_work)
-    Xb = [torch.rand((big.info.ncols, 8), dtype=torch.float64).pin_memory() for _ in range(2)]
-    rng = np.random.default_rng(9)
-    made = [_make(mats[:-1], rng) for _ in range(12)]
-    large = [srv.submit(len(mats) - 1, X, to_host=True) for X in Xb]
-    small = [srv.submit(mid, X, to_host=True) for mid, X in made]
-    for r in large + small:
-        r.wait(60)
-    st = srv.stats()
-    srv.stop()
-    assert max(r.t_launch for r in small) < large[1].t_launch, "small requests waited for the large ones"
-    assert "small" in st and "large" in st and st["small"]["requests"] == 12 and st["large"]["requests"] == 2
-    for r in large:
-        assert r.Y.numpy().tobytes() == _alone(big, r.X).numpy().tobytes()
-    assert_oracle_parity(hosts[-1], sell.SELL_F64, large[0].X.numpy(), large[0].Y.numpy(), what="large request")
-    for r in small:
-        assert r.Y.numpy().tobytes() == _alone(mats[r.mid], r.X).numpy().tobytes()
-        assert_oracle_parity(hosts[r.mid], mats[r.mid].info.store_type, r.X.numpy(), r.Y.numpy(),
-                             what=f"request {r.rid}")
