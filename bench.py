@@ -670,7 +670,13 @@ def batched_section(sell, autotune, model, stream, peak, gather_gps, nmat=512, k
                 shp_y = (h.info.nrows,) if k == 1 else (h.info.nrows, k)
                 items.append((h, torch.rand(shp_x, dtype=dt, device="cuda"),
                               torch.empty(shp_y, dtype=dt, device="cuda"), 0))
+            # the plan's launch (rows per block, right-hand-side block width)
+            # tuned on the plan itself; it changes no result
+            lt, ltable = autotune.tune_plan(items, k, stream=stream)
+            rflag = {8: 0, 4: sell.SELL_SPMV_RHS_BLOCK4}[lt["rhs"]]
+            items = [(h, X, Y, rflag) for h, X, Y, _ in items]
             plan = sell.sell_batch_create(items, stream=stream)
+            plan.set_launch(lt["tile"])
             plan.run(stream=stream)
             torch.cuda.synchronize()
             g = torch.cuda.CUDAGraph()
@@ -680,11 +686,11 @@ def batched_section(sell, autotune, model, stream, peak, gather_gps, nmat=512, k
             batch_y = [Y.clone() for _, _, Y, _ in items]
 
             def per_matrix():
-                for h, X, Y, _ in items:
+                for h, X, Y, fl in items:
                     if k == 1:
                         sell.sell_spmv(h, X, Y, stream=stream)
                     else:
-                        sell.sell_spmmv(h, X, Y, stream=stream)
+                        sell.sell_spmmv(h, X, Y, flags=fl, stream=stream)
             per_matrix()
             torch.cuda.synchronize()
             same = all(torch.equal(a, Y) for a, (_, _, Y, _) in zip(batch_y, items))
@@ -712,6 +718,9 @@ def batched_section(sell, autotune, model, stream, peak, gather_gps, nmat=512, k
                 gath += inf.nnz if kind == "lognormal" else 0
             t_bound = alg["banded"] / (peak * 1e9) + max(alg["lognormal"] / (peak * 1e9), gath / (gather_gps * 1e9))
             row[tag] = {"batch_ms": round(t_batch * 1e3, 3), "gflops": round(2.0 * nnz * k / t_batch / 1e9, 1),
+                        "tuned_launch": {"block": lt["tile"], "rhs_block": lt["rhs"]},
+                        "launch_candidates": [{"block": c["tile"], "rhs_block": c["rhs"], "us": round(c["us"], 1)}
+                                              for c in ltable],
                         "hbm_frac": round((alg["banded"] + alg["lognormal"]) / t_batch / 1e9 / peak, 4),
                         "class_bound_ms": round(t_bound * 1e3, 3), "class_bound_frac": round(t_bound / t_batch, 4),
                         "per_matrix_eager_ms": round(t_eager * 1e3, 3),
@@ -723,6 +732,27 @@ def batched_section(sell, autotune, model, stream, peak, gather_gps, nmat=512, k
             del g, g2, items
         row["f32_speedup_vs_f64"] = round(row["f64"]["batch_ms"] / row["f32"]["batch_ms"], 3)
         out[f"k{k}"] = row
+    # the banded half alone (regular, memory-bound matrices), binary32, k = 1
+    hb = [h for h, kind in zip(h32, kinds) if kind == "banded"]
+    items = [(h, torch.rand(h.info.ncols, dtype=torch.float32, device="cuda"),
+              torch.empty(h.info.nrows, dtype=torch.float32, device="cuda"), 0) for h in hb]
+    lt, _ = autotune.tune_plan(items, 1, stream=stream)
+    plan = sell.sell_batch_create(items, stream=stream)
+    plan.set_launch(lt["tile"])
+    plan.run(stream=stream)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        plan.run(stream=stream)
+    t_b = _time_graph(g, stream, 20)
+    alg_b = sum(model.algorithmic_bytes(h.info.nrows, h.info.ncols, h.info.nnz, h.info.nchunks, h.info.C, 4, 4,
+                                        h.info.has_perm) for h in hb)
+    nnz_b = sum(h.info.nnz for h in hb)
+    out["banded_only_f32_k1"] = {"matrices": len(hb), "nnz": nnz_b, "batch_ms": round(t_b * 1e3, 3),
+                                 "gflops": round(2.0 * nnz_b / t_b / 1e9, 1),
+                                 "hbm_frac": round(alg_b / t_b / 1e9 / peak, 4), "block": lt["tile"]}
+    plan.free()
+    del g, items
     for h in h32 + h64:
         h.free()
     torch.cuda.empty_cache()
@@ -907,6 +937,7 @@ def compact_summary(line, ex):
                                        "bound": g(b, f"k{k}", "f32", "class_bound_frac"),
                                        "x_f64": g(b, f"k{k}", "f32_speedup_vs_f64"),
                                        "ok": g(b, f"k{k}", "f32", "batch_equals_per_matrix")} for k in (1, 4, 8)}
+        s["batch512_f32"]["banded_only_k1_hbm"] = g(b, "banded_only_f32_k1", "hbm_frac")
     v = ex.get("serving")
     if isinstance(v, dict) and "load_0.5" in v:
         s["serving"] = {"sat_rps": v["saturated_req_per_s"]}

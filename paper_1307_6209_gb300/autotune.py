@@ -157,7 +157,7 @@ def build_tuned(A, choice: Choice, store_type: int = sell.SELL_F64, stream=None)
     return h
 
 
-def tune_batch(samples, store_type: int = sell.SELL_F32, Cs=(32, 64), sigmas=(1, 32, 256, 4096, 1 << 30),
+def tune_batch(samples, store_type: int = sell.SELL_F32, Cs=(32, 64), sigmas=(1, 32, 256, 2048, 4096, 1 << 30),
                reps: int = 10, stream=None):
     """Pick (C, sigma) for a class of matrices by the throughput of a batch.
 
@@ -186,4 +186,27 @@ def tune_batch(samples, store_type: int = sell.SELL_F32, Cs=(32, 64), sigmas=(1,
             plan.free()
             for h in hs:
                 h.free()
+    return best, table
+
+
+def tune_plan(items, k: int, tiles=(64, 128, 256), rhs=(8, 4), reps: int = 10, stream=None):
+    """Pick the launch of a whole batch plan by timing it: the block size
+    (rows per work unit, sell_batch_set_launch) and, for k >= 4 right-hand
+    sides, the widest block of right-hand sides (SELL_SPMV_RHS_BLOCK*).
+    Neither changes any result.  items: (handle, X, Y, flags) as for
+    sell_batch_create.  Returns (best {"tile", "rhs", "us"}, all candidates)."""
+    import torch
+
+    stream = stream or torch.cuda.current_stream()
+    flag = {8: 0, 4: sell.SELL_SPMV_RHS_BLOCK4, 2: sell.SELL_SPMV_RHS_BLOCK2, 1: sell.SELL_SPMV_RHS_BLOCK1}
+    best, table = None, []
+    for w in (rhs if k >= 4 else (8,)):
+        plan = sell.sell_batch_create([(h, X, Y, fl | flag[w]) for h, X, Y, fl in items], stream=stream)
+        for t in tiles:
+            plan.set_launch(t)
+            us = _time(lambda: plan.run(stream=stream), stream, reps)
+            table.append({"tile": t, "rhs": w, "us": us})
+            if best is None or us < best["us"]:
+                best = {"tile": t, "rhs": w, "us": us}
+        plan.free()
     return best, table

@@ -8,8 +8,15 @@
 //     budget - resident bytes -- the HBM budget is never exceeded;
 //   * packs the admitted ones into one batch plan (sell_batch.cu: one launch
 //     per kernel variant, every product bitwise the same as alone) on a free
-//     stream, with the host-to-device copies of the x blocks before it and
-//     the device-to-host copies of the results after it;
+//     stream, with the device-to-host copies of the results after it;
+//   * meters the host-to-device copies of the x blocks itself: copies on
+//     different streams share the copy engine first in, first out (a 64 KB
+//     copy issued after a 256 MB one on another stream finishes with it,
+//     1.3 ms later), so every input goes through one copy stream in chunks
+//     of kChunk bytes, at most kWindow bytes in flight, the batch with the
+//     fewest bytes left first; a batch's kernels are enqueued behind an event
+//     recorded after its last chunk.  A small request then waits for at
+//     most a window of chunks instead of a large request's whole input;
 //   * keeps up to `streams` batches in flight, so requests that arrive while
 //     others run are admitted as soon as a stream and memory are free and
 //     their work overlaps on the device;
@@ -56,10 +63,26 @@ struct Req {
     bool keep_y() const { return Y == nullptr; }
 };
 
+// Input copies are issued in chunks of at most kChunk bytes, at most
+// kWindow bytes in flight on the copy stream (about 160 us at 200 GB/s).
+constexpr size_t kChunk = 4u << 20;
+constexpr size_t kWindow = 32u << 20;
+
+struct Chunk {
+    char *dst;
+    const char *src;
+    size_t bytes;
+};
+
 struct Batch {
     int si = 0;
     sell_batch *plan = nullptr;
     std::vector<Req *> reqs;
+    std::vector<Chunk> chunks;  // its host-to-device copies, in order
+    size_t next = 0;            // the next chunk to issue
+    size_t left = 0;            // bytes not yet issued
+    bool launched = false;      // kernels, result copies and completion event enqueued
+    sell_status status = SELL_OK;
 };
 
 bool is_pinned_host(const void *p) {
@@ -85,6 +108,11 @@ struct sell_server {
     sell::Arena arena;
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> events;  // one per stream (a stream holds at most one batch)
+    std::vector<cudaEvent_t> ready;   // one per stream: its batch's input copies issued (on h2d)
+    cudaStream_t h2d = nullptr;       // the copy stream of every input
+    std::deque<std::pair<cudaEvent_t, size_t>> copying;  // chunks in flight on h2d (event after each)
+    std::vector<cudaEvent_t> spare;   // chunk events to reuse
+    size_t copy_bytes = 0;            // bytes in flight on h2d
     std::deque<int> free_streams;
     std::vector<sell::Batch> inflight;
     std::mutex mu;
@@ -151,53 +179,119 @@ void release_y(sell_server *S, Req *r) {
     r->reserved = false;
 }
 
-// Issue one batch on stream si (called without the lock; the requests are
-// owned by the scheduler until they are marked done).
-void launch(sell_server *S, int si, std::vector<Req *> &batch, Batch &B) {
-    cudaStream_t st = S->streams[si];
+// Admit a batch on stream si: stamp its requests and list its input copies
+// in chunks (no CUDA call; the scheduler thread owns the batch from here).
+void prepare(sell_server *S, int si, std::vector<Req *> &batch, Batch &B) {
     const double t = now_s();
     const int n = (int)batch.size();
-    std::vector<sell_batch_item> items(n);
-    std::vector<void *> scr(n, nullptr);
-    sell_status status = SELL_OK;
+    B.si = si;
+    B.reqs = batch;
+    auto add = [&](char *dst, const void *src, size_t bytes) {
+        const char *s = static_cast<const char *>(src);
+        for (size_t o = 0; o < bytes; o += kChunk) {
+            const size_t c = std::min(kChunk, bytes - o);
+            B.chunks.push_back({dst + o, s + o, c});
+            B.left += c;
+        }
+    };
     for (int i = 0; i < n; ++i) {
         Req *r = batch[i];
         r->tl = t;
         r->batch = n;
-        sell_matrix *h = S->mats[r->mid];
-        char *xd = S->arena_base + r->xoff, *yd = S->arena_base + r->yoff;
-        if (r->xb && status == SELL_OK &&
-            cudaMemcpyAsync(xd, r->X, r->xb, cudaMemcpyHostToDevice, st) != cudaSuccess)
-            status = cuda_fail(cudaGetLastError(), "server: input copy");
-        if ((r->flags & SELL_SPMV_ACCUMULATE) && r->yb && status == SELL_OK &&
-            cudaMemcpyAsync(yd, r->Y, r->yb, cudaMemcpyHostToDevice, st) != cudaSuccess)
-            status = cuda_fail(cudaGetLastError(), "server: accumulate copy");
-        items[i].A = h;
-        items[i].X = xd;
-        items[i].Y = yd;
+        if (r->xb) add(S->arena_base + r->xoff, r->X, r->xb);
+        if ((r->flags & SELL_SPMV_ACCUMULATE) && r->yb) add(S->arena_base + r->yoff, r->Y, r->yb);
+    }
+}
+
+// Enqueue a batch whose input copies have all been issued: its stream waits
+// for them, then runs the plan, the result copies and the completion event
+// (called without the lock).
+void finish_launch(sell_server *S, Batch &B) {
+    const int si = B.si;
+    cudaStream_t st = S->streams[si];
+    const int n = (int)B.reqs.size();
+    sell_status status = B.status;
+    if (status == SELL_OK && !B.chunks.empty() &&
+        (cudaEventRecord(S->ready[si], S->h2d) != cudaSuccess || cudaStreamWaitEvent(st, S->ready[si], 0) != cudaSuccess))
+        status = cuda_fail(cudaGetLastError(), "server: input copy ordering");
+    std::vector<sell_batch_item> items(n);
+    std::vector<void *> scr(n, nullptr);
+    for (int i = 0; i < n; ++i) {
+        Req *r = B.reqs[i];
+        items[i].A = S->mats[r->mid];
+        items[i].X = S->arena_base + r->xoff;
+        items[i].Y = S->arena_base + r->yoff;
         items[i].ldx = r->k;
         items[i].ldy = r->k;
         items[i].k = r->k;
         items[i].flags = r->flags;
         scr[i] = r->sb ? S->arena_base + r->soff : nullptr;
     }
-    B.si = si;
-    B.reqs = batch;
-    B.plan = new (std::nothrow) sell_batch();
-    if (!B.plan && status == SELL_OK) status = SELL_ENOMEM;
+    if (status == SELL_OK) {
+        B.plan = new (std::nothrow) sell_batch();
+        if (!B.plan) status = SELL_ENOMEM;
+    }
     if (status == SELL_OK) status = batch_create(items.data(), n, st, B.plan, scr.data());
     if (status == SELL_OK) status = batch_run(B.plan, 0, st);
     for (int i = 0; i < n && status == SELL_OK; ++i) {
-        Req *r = batch[i];
+        Req *r = B.reqs[i];
         if (!r->keep_y() && r->yb &&
             cudaMemcpyAsync(r->Y, S->arena_base + r->yoff, r->yb, cudaMemcpyDeviceToHost, st) != cudaSuccess)
             status = cuda_fail(cudaGetLastError(), "server: result copy");
     }
     if (status != SELL_OK)
-        for (Req *r : batch) r->status = status;
+        for (Req *r : B.reqs) r->status = status;
     if (cudaEventRecord(S->events[si], st) != cudaSuccess) {
         (void)cudaGetLastError();
         (void)cudaStreamSynchronize(st);
+    }
+    B.launched = true;
+}
+
+// Feed the copy stream (called without the lock, scheduler thread only):
+// retire the chunks that have landed, launch the batches whose copies are
+// all issued, and issue further chunks while the window has room -- always
+// from the batch with the fewest bytes left (the earliest admitted on ties).
+void pump(sell_server *S) {
+    while (!S->copying.empty()) {
+        const cudaError_t q = cudaEventQuery(S->copying.front().first);
+        if (q == cudaErrorNotReady) break;
+        if (q != cudaSuccess) (void)cudaGetLastError();  // the batch's own event reports the failure
+        S->copy_bytes -= S->copying.front().second;
+        S->spare.push_back(S->copying.front().first);
+        S->copying.pop_front();
+    }
+    for (;;) {
+        Batch *pick = nullptr;
+        for (Batch &B : S->inflight) {
+            if (B.launched) continue;
+            if (B.next == B.chunks.size()) {
+                finish_launch(S, B);
+                continue;
+            }
+            if (!pick || B.left < pick->left) pick = &B;
+        }
+        if (!pick || S->copy_bytes >= kWindow) return;
+        const Chunk &c = pick->chunks[pick->next];
+        cudaEvent_t ev = nullptr;
+        if (!S->spare.empty()) {
+            ev = S->spare.back();
+            S->spare.pop_back();
+        } else if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            ev = nullptr;
+        }
+        if (!ev || cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyHostToDevice, S->h2d) != cudaSuccess ||
+            cudaEventRecord(ev, S->h2d) != cudaSuccess) {
+            pick->status = cuda_fail(cudaGetLastError(), "server: input copy");
+            if (ev) S->spare.push_back(ev);
+            pick->next = pick->chunks.size();  // no further copies; the batch reports the failure
+            pick->left = 0;
+            continue;
+        }
+        S->copying.push_back({ev, c.bytes});
+        S->copy_bytes += c.bytes;
+        pick->next += 1;
+        pick->left -= c.bytes;
     }
 }
 
@@ -209,6 +303,10 @@ void scheduler(sell_server *S) {
         bool retired = false;
         for (size_t i = 0; i < S->inflight.size();) {
             Batch &B = S->inflight[i];
+            if (!B.launched) {  // still waiting for its input copies
+                ++i;
+                continue;
+            }
             const cudaError_t q = cudaEventQuery(S->events[B.si]);
             if (q == cudaErrorNotReady) {
                 ++i;
@@ -238,7 +336,7 @@ void scheduler(sell_server *S) {
         // next requests in order, those whose work is within the ratio of it
         // (the others wait for the next batch, on another stream), so small
         // requests do not wait for the end of a large one's launch.
-        if (!S->free_streams.empty() && !S->queue.empty()) {
+        while (!S->free_streams.empty() && !S->queue.empty()) {
             std::vector<Req *> batch;
             if (S->size_ratio <= 1) {
                 double bw = 0;  // the batch's work so far
@@ -275,20 +373,21 @@ void scheduler(sell_server *S) {
                     }
                 }
             }
-            if (!batch.empty()) {
-                const int si = S->free_streams.front();
-                S->free_streams.pop_front();
-                Batch B;
-                lk.unlock();
-                launch(S, si, batch, B);
-                lk.lock();
-                // (requests of a batch are retired together once its event passed)
-                S->inflight.push_back(std::move(B));
-                S->nbatch += 1;
-                S->nbatched += (int64_t)batch.size();
-                continue;
-            }
+            if (batch.empty()) break;
+            const int si = S->free_streams.front();
+            S->free_streams.pop_front();
+            Batch B;
+            prepare(S, si, batch, B);
+            // (requests of a batch are retired together once its event passed)
+            S->inflight.push_back(std::move(B));
+            S->nbatch += 1;
+            S->nbatched += (int64_t)batch.size();
         }
+        // the copies and launches happen without the lock: only this thread
+        // touches the batches in flight and the copy stream
+        lk.unlock();
+        pump(S);
+        lk.lock();
         if (S->stop && S->queue.empty() && S->inflight.empty()) break;
         if (S->inflight.empty())
             S->cv_work.wait(lk);  // idle: until a submit, a release or stop
@@ -375,21 +474,31 @@ sell_status sell_server_create(const sell_handle *mats, int32_t n, const sell_se
     sell_status st = SELL_OK;
     for (int i = 0; i < S->nstreams && st == SELL_OK; ++i) {
         cudaStream_t s = nullptr;
-        cudaEvent_t e = nullptr;
+        cudaEvent_t e = nullptr, rd = nullptr;
         if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+            cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&rd, cudaEventDisableTiming) != cudaSuccess)
             st = cuda_fail(cudaGetLastError(), "sell_server_create: stream/event");
         S->streams.push_back(s);
         S->events.push_back(e);
+        S->ready.push_back(rd);
         S->free_streams.push_back(i);
     }
+    if (st == SELL_OK && cudaStreamCreateWithFlags(&S->h2d, cudaStreamNonBlocking) != cudaSuccess)
+        st = cuda_fail(cudaGetLastError(), "sell_server_create: copy stream");
     if (st == SELL_OK && cudaDeviceSynchronize() != cudaSuccess)
         st = cuda_fail(cudaGetLastError(), "sell_server_create: arena");
-    if (st != SELL_OK) {
-        for (auto s : S->streams)
+    auto destroy_cuda = [](sell_server *T) {
+        for (auto s : T->streams)
             if (s) (void)cudaStreamDestroy(s);
-        for (auto e : S->events)
+        if (T->h2d) (void)cudaStreamDestroy(T->h2d);
+        for (auto e : T->events)
             if (e) (void)cudaEventDestroy(e);
+        for (auto e : T->ready)
+            if (e) (void)cudaEventDestroy(e);
+    };
+    if (st != SELL_OK) {
+        destroy_cuda(S);
         S->al.put(S->arena_base, nullptr);
         delete S;
         return st;
@@ -397,8 +506,7 @@ sell_status sell_server_create(const sell_handle *mats, int32_t n, const sell_se
     try {
         S->thr = std::thread(scheduler, S);
     } catch (...) {
-        for (auto s : S->streams) (void)cudaStreamDestroy(s);
-        for (auto e : S->events) (void)cudaEventDestroy(e);
+        destroy_cuda(S);
         S->al.put(S->arena_base, nullptr);
         delete S;
         return fail(SELL_ENOMEM, "sell_server_create: cannot start the scheduler thread");
@@ -549,8 +657,13 @@ sell_status sell_server_destroy(sell_server_t S) {
     S->cv_work.notify_all();
     if (S->thr.joinable()) S->thr.join();
     for (auto s : S->streams) (void)cudaStreamSynchronize(s);
+    if (S->h2d) (void)cudaStreamSynchronize(S->h2d);
     for (auto s : S->streams) (void)cudaStreamDestroy(s);
+    if (S->h2d) (void)cudaStreamDestroy(S->h2d);
     for (auto e : S->events) (void)cudaEventDestroy(e);
+    for (auto e : S->ready) (void)cudaEventDestroy(e);
+    for (auto &ce : S->copying) (void)cudaEventDestroy(ce.first);
+    for (auto e : S->spare) (void)cudaEventDestroy(e);
     S->al.put(S->arena_base, nullptr);
     (void)cudaDeviceSynchronize();
     for (auto &kv : S->reqs) delete kv.second;

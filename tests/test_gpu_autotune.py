@@ -64,3 +64,32 @@ def test_profile_case_batch_runs(capsys):
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert line["batch"] == 4 and line["k"] == 4 and line["us"] > 0
     assert 0 < line["beta"] <= 1 and line["nnz"] <= line["stored"]
+
+
+def test_tune_plan_measures_every_launch_and_keeps_the_bits():
+    """tune_plan times every (block size, right-hand-side width) of a batch
+    plan and returns one of them; the plan run with the choice gives the
+    same bits as the default plan."""
+    import torch
+    from paper_1307_6209_gb300 import autotune, sell
+
+    hs = [sell.sell_build(synth.banded(3000 + 500 * i, seed=i), C=32, sigma=256, store_type=sell.SELL_F32)
+          for i in range(6)]
+    k = 8
+    items = [(h, torch.rand((h.info.ncols, k), dtype=torch.float32, device="cuda"),
+              torch.empty((h.info.nrows, k), dtype=torch.float32, device="cuda"), 0) for h in hs]
+    best, table = autotune.tune_plan(items, k, reps=2)
+    assert {(c["tile"], c["rhs"]) for c in table} == {(t, w) for t in (64, 128, 256) for w in (8, 4)}
+    assert best["us"] == min(c["us"] for c in table)
+    plan = sell.sell_batch_create(items)
+    plan.run()
+    torch.cuda.synchronize()
+    ref = [Y.clone() for _, _, Y, _ in items]
+    flag = {8: 0, 4: sell.SELL_SPMV_RHS_BLOCK4}[best["rhs"]]
+    tuned = sell.sell_batch_create([(h, X, Y, flag) for h, X, Y, _ in items])
+    tuned.set_launch(best["tile"])
+    for _, _, Y, _ in items:
+        Y.fill_(float("nan"))
+    tuned.run()
+    torch.cuda.synchronize()
+    assert all(torch.equal(Y, r) for (_, _, Y, _), r in zip(items, ref))

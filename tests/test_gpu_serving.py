@@ -286,3 +286,35 @@ def test_wait_and_next_racing_for_one_request():
     finally:
         sell.sell_server_destroy(srv)
         h.free()
+
+
+def test_small_inputs_are_copied_ahead_of_a_large_one():
+    """Input copies on different streams share the copy engine first in,
+    first out, so the server meters them: a large request's 128 MB input goes
+    in chunks, and the inputs of small requests submitted just after it are
+    copied between its chunks -- they complete before it does.  Every result
+    is still the request alone, and the oracle's product within its bound."""
+    import torch
+    from paper_1307_6209_gb300 import serving, sell
+    Abig = synth.lognormal_device(2_000_000, seed=16)
+    big = sell.sell_build(Abig, C=32, sigma=2_000_000)
+    hosts = []
+    mats = _mats(seed=90, hosts=hosts) + [big]
+    hosts.append(host_csr(Abig))
+    del Abig
+    srv = serving.Server(mats, hbm_budget_bytes=sum(m.info.device_bytes for m in mats) + (4 << 30), max_batch=8,
+                         streams=4)
+    Xb = torch.rand((big.info.ncols, 8), dtype=torch.float64).pin_memory()
+    rng = np.random.default_rng(10)
+    small_x = [torch.rand(mats[0].info.ncols, dtype=torch.float64).pin_memory() for _ in range(6)]
+    large = srv.submit(len(mats) - 1, Xb, to_host=True)
+    small = [srv.submit(0, x, to_host=True) for x in small_x]
+    for r in [large] + small:
+        r.wait(60)
+    srv.stop()
+    assert min(r.t_done for r in small) < large.t_done, "every small request waited for the large input"
+    assert large.Y.numpy().tobytes() == _alone(big, Xb).numpy().tobytes()
+    assert_oracle_parity(hosts[-1], sell.SELL_F64, Xb.numpy(), large.Y.numpy(), what="large request")
+    for r in small:
+        assert r.Y.numpy().tobytes() == _alone(mats[0], r.X).numpy().tobytes()
+        assert_oracle_parity(hosts[0], mats[0].info.store_type, r.X.numpy(), r.Y.numpy(), what=f"request {r.rid}")
