@@ -380,19 +380,31 @@ def measure_gather(sell, stream, n_words, reps=5, iters=64):
     return grid * 256 * iters * 8 / best / 1e9
 
 
-def measure_fp64_fma(sell, stream, iters=2000):
+def measure_fp64_fma(sell, stream, iters=6000, clocks=None):
+    """Binary64 FMA rate of sell_bench_fma64 over about 0.2 s, and the median
+    SM clock sampled meanwhile (a kernel of nothing but FMAs may draw enough
+    power to run below the maximum clock; the rate scaled to the maximum
+    clock is what an SpMV running at that clock can reach)."""
     import torch
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     grid = sms * 8
     sink = torch.empty(grid * 256, dtype=torch.float64, device="cuda")
     sell.sell_bench_fma64(sink, grid, 10, stream=stream)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
     a.record(stream)
     sell.sell_bench_fma64(sink, grid, iters, stream=stream)
     b.record(stream)
     b.synchronize()
+    t1 = time.perf_counter()
     fmas = grid * 256 * iters * 64
-    return 2.0 * fmas / (a.elapsed_time(b) * 1e-3) / 1e12
+    tf = 2.0 * fmas / (a.elapsed_time(b) * 1e-3) / 1e12
+    out = {"tflops": round(tf, 4)}
+    cs = clocks.summary(t0, t1) if clocks is not None else None
+    if cs and cs.get("sm_mhz") and cs.get("sm_max_mhz"):
+        out.update({"sm_mhz": cs["sm_mhz"], "sm_max_mhz": cs["sm_max_mhz"], "samples": cs["samples"],
+                    "tflops_at_max_clock": round(tf * cs["sm_max_mhz"] / cs["sm_mhz"], 4)})
+    return out
 
 
 def cpu_baseline(A, x, what, target_s=10.0):
@@ -1028,7 +1040,8 @@ def run_ours(args):
         # ---- measuring kernels: read bandwidth b, random-gather rate, FP64 FMA peak
         b_read = measure_read_bw(sell, stream)
         gather_gps = measure_gather(sell, stream, 2_000_000)
-        fma_tf = measure_fp64_fma(sell, stream)
+        fma = measure_fp64_fma(sell, stream, clocks=nvml)
+        fma_tf = fma.get("tflops_at_max_clock", fma["tflops"])
 
         # ---- autotuner: stage 1 = the (C, sigma) candidates, stage 2 = launch shapes
         if args.C is not None or args.sigma is not None or args.no_sweep:
@@ -1202,6 +1215,7 @@ def run_ours(args):
     extras["b_read_gbs"] = round(b_read, 1)
     extras["gather_peak_ggps"] = round(gather_gps, 1)
     extras["fp64_fma_peak_tflops"] = round(fma_tf, 3)
+    extras["fp64_fma_bench"] = fma
     extras["fp64_pipe_frac"] = round(flops / kern_s / 1e12 / fma_tf, 4)
     extras["build_ms"] = round(build_ms, 2)
     extras["tuned"] = {"C": C, "sigma": sigma, "block": best.block, "unroll": best.unroll,

@@ -16,6 +16,11 @@ matrices with rows uniform in [1000, 200000] (seeded), even ones banded
 (bandwidth 64, 7-30 entries per row) and odd ones lognormal (`--kinds banded`
 or `lognormal`: one kind only), all in the given (C, sigma) and storage type,
 each with its own k right-hand sides.
+
+    python -m paper_1307_6209_gb300.profile_case --measure gathers   (or copies)
+
+measures the random-gather rates of the load/store path and of TMA gather4,
+or how host-to-device copies on two streams share the copy engine.
 """
 from __future__ import annotations
 
@@ -45,7 +50,15 @@ def main(argv=None):
     p.add_argument("--kinds", choices=["mixed", "banded", "lognormal"], default="mixed",
                    help="batch matrices: alternating banded / lognormal, or one kind only")
     p.add_argument("--tile", type=int, default=0, help="batch block size (64, 128, 256; 0 keeps the default)")
+    p.add_argument("--measure", choices=["gathers", "copies"], default=None,
+                   help="gathers: random-gather rates of the load/store path and of TMA gather4 "
+                        "(sell_bench_gather / sell_bench_gather4); copies: a small host-to-device copy "
+                        "issued after a large one on another stream")
     a = p.parse_args(argv)
+    if a.measure == "gathers":
+        return run_gathers()
+    if a.measure == "copies":
+        return run_copies()
     if a.batch > 0:
         return run_batch(a)
 
@@ -148,6 +161,102 @@ def run_batch(a):
     plan.free()
     for h, _, _, _ in items:
         h.free()
+    return 0
+
+
+def _best_ms(fn, stream, reps=5):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    best = 1e30
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        best = min(best, a.elapsed_time(b))
+    return best
+
+
+def run_gathers():
+    """Random sectors per second from an L2-resident x through the load/store
+    path (8-byte words) and through TMA gather4 (16-byte rows, four per copy)."""
+    import torch
+
+    from . import sell
+    sell.load()
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    s = torch.cuda.Stream()
+    out = []
+    for nw in (2_000_000, 8_000_000):
+        x = torch.ones(nw, dtype=torch.int64, device="cuda")
+        grid, iters = sms * 8, 64
+        sink = torch.zeros(grid * 256, dtype=torch.float64, device="cuda")
+        ms = _best_ms(lambda: sell.sell_bench_gather(x, nw, sink, grid, iters, stream=s), s)
+        out.append({"kernel": "k_gather", "n_words": nw, "grid": grid, "threads": 256, "iters": iters,
+                    "G_per_s": round(grid * 256 * iters * 8 / ms / 1e6, 1)})
+        for bps in (2, 4, 7):
+            for iters in (64, 256):
+                grid = sms * bps
+                sink = torch.zeros(grid * 128 + 1, dtype=torch.float64, device="cuda")
+                ms = _best_ms(lambda: sell.sell_bench_gather4(x, nw, sink, grid, iters, stream=s), s)
+                out.append({"kernel": "k_gather4", "n_words": nw, "grid": grid, "threads": 128, "iters": iters,
+                            "G_per_s": round(grid * 128 * iters * 4 / ms / 1e6, 1),
+                            "wait_gave_up": bool(sink[-1].item() != 0)})
+        del x
+    print(json.dumps(out))
+    return 0
+
+
+def run_copies():
+    """A 64 KB host-to-device copy issued right after a 256 MB one on another
+    stream: when does it complete?  (And the small copy alone, and two large
+    copies on two streams.)"""
+    import torch
+    big_h = torch.rand(32 * 2 ** 20, dtype=torch.float64).pin_memory()
+    big_d = torch.empty_like(big_h, device="cuda")
+    small_h = torch.rand(8192, dtype=torch.float64).pin_memory()
+    small_d = torch.empty_like(small_h, device="cuda")
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    out = {"trials": []}
+    for _ in range(3):
+        torch.cuda.synchronize()
+        e0, ea, eb = ev(), ev(), ev()
+        e0.record(sa)
+        with torch.cuda.stream(sa):
+            big_d.copy_(big_h, non_blocking=True)
+        ea.record(sa)
+        sb.wait_event(e0)
+        with torch.cuda.stream(sb):
+            small_d.copy_(small_h, non_blocking=True)
+        eb.record(sb)
+        torch.cuda.synchronize()
+        out["trials"].append({"large_done_ms": round(e0.elapsed_time(ea), 3),
+                              "small_done_ms": round(e0.elapsed_time(eb), 3)})
+    e0, e1 = ev(), ev()
+    e0.record(sb)
+    with torch.cuda.stream(sb):
+        small_d.copy_(small_h, non_blocking=True)
+    e1.record(sb)
+    torch.cuda.synchronize()
+    out["small_alone_ms"] = round(e0.elapsed_time(e1), 4)
+    big_h2 = torch.rand(32 * 2 ** 20, dtype=torch.float64).pin_memory()
+    big_d2 = torch.empty_like(big_h2, device="cuda")
+    e0, e1, e2 = ev(), ev(), ev()
+    e0.record(sa)
+    sb.wait_event(e0)
+    with torch.cuda.stream(sa):
+        big_d.copy_(big_h, non_blocking=True)
+    with torch.cuda.stream(sb):
+        big_d2.copy_(big_h2, non_blocking=True)
+    e1.record(sa)
+    e2.record(sb)
+    torch.cuda.synchronize()
+    out["two_large_done_ms"] = [round(e0.elapsed_time(e1), 3), round(e0.elapsed_time(e2), 3)]
+    out["large_gbs"] = round(big_h.numel() * 8 / (out["trials"][-1]["large_done_ms"] * 1e-3) / 1e9, 1)
+    print(json.dumps(out))
     return 0
 
 
