@@ -135,7 +135,7 @@ def kernel_name(best, C, inf):
     """The binary64 SpMV kernel the tuned launch runs."""
     long_rows = "true" if inf.max_row_len > 64 else "false"
     if best.pipeline == 2:
-        ring = {1: 2, 2: 2, 4: 3, 8: 4}[best.unroll]
+        ring = {1: 1, 2: 2, 4: 3, 8: 4}[best.unroll]
         return (f"k_spmv_bulk<double,Plain<double>,{C // 32},{long_rows}> {best.block // 32} warps/block, "
                 f"{ring} pieces per warp")
     return (f"k_spmmv<double,1,{best.unroll},{'true' if best.pipeline else 'false'},Plain<double>,{long_rows}> "

@@ -253,8 +253,8 @@ SELL_API sell_status sell_spmmv_noalloc(sell_handle h, const void *X, int64_t ld
  *            2 bulk-staged: each warp copies whole pieces of its chunks into
  *              shared memory with asynchronous bulk copies while it multiplies
  *              the previous piece (single right-hand sides; C = 32, 64 or 128;
- *              block = warps per block x 32, unroll 1/2/4/8 = 2/2/3/4 pieces
- *              in flight per warp).  Selecting it computes the per-warp work
+ *              block = warps per block x 32, unroll 1/2/4/8 = 1/2/3/4 pieces
+ *              per warp; with 1 the next copy starts when the piece is used).  Selecting it computes the per-warp work
  *              split of the handle on the device (synchronous; a few small
  *              allocations through the handle's allocator).
  * Errors: SELL_EINVAL (values), SELL_EUNSUPPORTED (pipeline 2 with another

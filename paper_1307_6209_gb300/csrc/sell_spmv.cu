@@ -82,7 +82,7 @@ sell_status launch_block_with_scratch(const sell_matrix *h, const void *X, int64
 }
 
 // Launch shape and work split of the bulk-staged SpMV for the handle's
-// block (warps per block) and unroll (slots per warp: 2, 2, 3, 4 for unroll
+// block (warps per block) and unroll (slots per warp: 1, 2, 3, 4 for unroll
 // 1, 2, 4, 8; fewer if shared memory does not hold them): one persistent
 // wave, every SM filled with as many blocks as fit.
 sell_status bulk_prepare(sell_matrix *h) {
@@ -93,9 +93,9 @@ sell_status bulk_prepare(sell_matrix *h) {
     if (((uintptr_t)h->val | (uintptr_t)h->col | (uintptr_t)h->srl) % 16 != 0)
         return fail(SELL_EUNSUPPORTED, "bulk-staged SpMV needs 16-byte aligned format arrays");
     const int W = h->block / 32;
-    int R = h->unroll >= 8 ? 4 : (h->unroll >= 4 ? 3 : 2);
+    int R = h->unroll >= 8 ? 4 : (h->unroll >= 4 ? 3 : (h->unroll >= 2 ? 2 : 1));
     int bps = 0;
-    for (; R >= 2; --R) {
+    for (; R >= 1; --R) {
         switch (h->store_type) {
             case SELL_F64: bps = bulk_blocks_per_sm_f64(h, W, R); break;
             case SELL_F32: bps = bulk_blocks_per_sm_f32(h, W, R); break;

@@ -23,7 +23,8 @@
 // Pipeline per warp (R slots of kStageElems elements): lane 0 issues the copy
 // of piece k + R - 1 into the slot that piece k - 1 used, then all lanes wait
 // for piece k, gather x for all its entries at once, and run the FMA chains
-// in entry order.  Every wait is bounded (kWaitNs); a wait that gives up sets
+// in entry order.  With R = 1 (one piece per warp, twice the resident warps
+// of R = 2) the next piece is issued once the current one is consumed.  Every wait is bounded (kWaitNs); a wait that gives up sets
 // *dstat, waits (bounded) for the warp's copies still in flight and ends the
 // warp, and sell_check reports it.  For testing that route, a launch may ask
 // (Args::expire_ns) that the first warp of the grid first waits, with that
@@ -225,7 +226,7 @@ __global__ void __launch_bounds__(512) k_spmv_bulk(const __grid_constant__ Args<
         }
     };
 
-    for (int i = 0; i < R - 1; ++i)
+    for (int i = 0; i < (R > 1 ? R - 1 : 1); ++i)
         if (!issue_next()) break;
     __syncwarp();
 
@@ -248,7 +249,7 @@ __global__ void __launch_bounds__(512) k_spmv_bulk(const __grid_constant__ Args<
         out[q] = -1;
     }
     for (int64_t k = 0; k < issued; ++k) {
-        issue_next();  // piece k + R - 1 into the slot of piece k - 1
+        if (R > 1) issue_next();  // piece k + R - 1 into the slot of piece k - 1
         const int slot = (int)(k % R);
         bool ok = true;
         if (a.expire_ns && k == 0 && wg == 0) ok = mbar_wait(never, 0, a.expire_ns);  // runs out
@@ -294,6 +295,7 @@ __global__ void __launch_bounds__(512) k_spmv_bulk(const __grid_constant__ Args<
                 if (out[q] >= 0) a.Y[out[q] * a.ldy] = acc[q].result();
         }
         __syncwarp();
+        if (R == 1) issue_next();  // the one slot is free again: piece k + 1
     }
 }
 

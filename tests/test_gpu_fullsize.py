@@ -26,7 +26,8 @@ def lognormal2m():
 
 @pytest.mark.parametrize("C,sigma,block,unroll,pipe", [(64, 2_000_000, 128, 4, 1), (32, 2_000_000, 128, 8, 0),
                                                        (32, 1, 256, 4, 1), (128, 4096, 128, 2, 0),
-                                                       (32, 2_000_000, 256, 2, 2), (128, 2_000_000, 512, 4, 2)])
+                                                       (32, 2_000_000, 256, 2, 2), (128, 2_000_000, 512, 4, 2),
+                                                       (128, 2_000_000, 512, 1, 2)])
 def test_lognormal_2m_full(lognormal2m, C, sigma, block, unroll, pipe):
     import torch
     from paper_1307_6209_gb300 import sell
