@@ -159,6 +159,13 @@ SELL_API sell_status sell_build(const sell_csr *A, const sell_opts *opts, void *
                                           SELL_SPMV_COMPENSATED takes precedence */
 #define SELL_SPMV_COMPENSATED 0x2u  /* F32/BF16 storage: compensated (Dot2)
                                        binary32 accumulation of each row */
+#define SELL_SPMV_HOST_DIRECT 0x80u /* X and Y are page-locked host memory that
+                                       the kernels read and write in place, over
+                                       the host link, with no staging copies (on
+                                       GB300 the x gather then mostly hits L2
+                                       and y streams out).  The same arithmetic,
+                                       so the same bits, as device buffers.
+                                       Exclusive with SELL_SPMV_HOST_IO */
 #define SELL_SPMV_RHS_BLOCK4 0x10u  /* SpMMV and batch items: multiply the right-hand
                                        sides in blocks of at most 4 (default 8);
                                        one of RHS_BLOCK4/2/1, the smallest wins.
@@ -169,7 +176,7 @@ SELL_API sell_status sell_build(const sell_csr *A, const sell_opts *opts, void *
 #define SELL_SPMV_RHS_BLOCK1 0x40u  /* ... one at a time */
 #define SELL_SPMV_HOST_IO 0x4u      /* x and y (X and Y) are host pointers
                                        (pinned for asynchronous copies); the
-                                       copies to and from the handle's two
+                                       copies to and from the handle's four
                                        staging slots, used in turn, are issued
                                        on `stream`.  Host-io products of one
                                        handle run one after another whatever

@@ -118,10 +118,13 @@ void free_matrix(sell_matrix *h) {
     // every kernel that may still read the arrays must finish first
     (void)cudaDeviceSynchronize();
     void *ptrs[] = {h->val,    h->col,   h->cs,   h->cl,     h->srl,    h->perm,
-                    h->lchunk, h->lunit, h->cnt, h->cnt2, h->part, h->io[0].x, h->io[0].y,
-                    h->io[1].x, h->io[1].y, h->bsc, h->wsplit, h->dstat, h->dot_part,
+                    h->lchunk, h->lunit, h->cnt, h->cnt2, h->part, h->bsc, h->wsplit, h->dstat, h->dot_part,
                     h->lrow,   h->lmeta};
     for (void *p : ptrs) h->al.put(p, nullptr);
+    for (auto &sl : h->io) {
+        h->al.put(sl.x, nullptr);
+        h->al.put(sl.y, nullptr);
+    }
     for (auto &sl : h->io)
         if (sl.done) (void)cudaEventDestroy(sl.done);
     if (h->kdone) (void)cudaEventDestroy(h->kdone);
@@ -130,6 +133,24 @@ void free_matrix(sell_matrix *h) {
     (void)cudaDeviceSynchronize();
     delete h;
     if (own_pool) trim_library_pool(dev);
+}
+
+// The device address of a page-locked host buffer (SELL_SPMV_HOST_DIRECT);
+// anything else is refused.
+sell_status host_device_pointer(const void *p, void **out, const char *name) {
+    if (!p) {
+        *out = nullptr;
+        return SELL_OK;
+    }
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(SELL_EINVAL, std::string("HOST_DIRECT: ") + name + " is not page-locked host memory");
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer)
+        return fail(SELL_EINVAL, std::string("HOST_DIRECT: ") + name + " is not page-locked host memory");
+    *out = a.devicePointer;
+    return SELL_OK;
 }
 
 // Grow a staging buffer of a slot whose previous use has been waited for.
@@ -189,17 +210,26 @@ sell_status sell_spmmv(sell_handle h, const void *X, int64_t ldx, void *Y, int64
                        uint32_t flags, void *stream) {
     if (!h) return fail(SELL_EINVAL, "sell_spmmv: NULL handle");
     if (k < 1 || ldx < k || ldy < k) return fail(SELL_EINVAL, "sell_spmmv: need k >= 1, ldx >= k, ldy >= k");
-    if (flags & ~(SELL_SPMV_ACCUMULATE | kCompFlags | kRhsFlags | SELL_SPMV_HOST_IO))
+    if (flags & ~(SELL_SPMV_ACCUMULATE | kCompFlags | kRhsFlags | SELL_SPMV_HOST_IO | SELL_SPMV_HOST_DIRECT))
         return fail(SELL_EINVAL, "sell_spmmv: unknown flags");
+    if ((flags & SELL_SPMV_HOST_IO) && (flags & SELL_SPMV_HOST_DIRECT))
+        return fail(SELL_EINVAL, "sell_spmmv: HOST_IO and HOST_DIRECT are exclusive");
     if ((flags & kCompFlags) && h->store_type == SELL_F64)
         return fail(SELL_EUNSUPPORTED, "compensated accumulation needs F32/BF16 storage");
     if (h->nrows == 0) return SELL_OK;
     if (!Y || (!X && h->ncols > 0)) return fail(SELL_EINVAL, "sell_spmmv: NULL vector");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (flags & SELL_SPMV_HOST_DIRECT) {
+        // page-locked host buffers, read and written in place by the kernels
+        void *xd = nullptr, *yd = nullptr;
+        SELL_TRY(host_device_pointer(X, &xd, "X"));
+        SELL_TRY(host_device_pointer(Y, &yd, "Y"));
+        return launch_spmmv(h, xd, ldx, yd, ldy, k, flags & ~SELL_SPMV_HOST_DIRECT, s);
+    }
     if (!(flags & SELL_SPMV_HOST_IO)) return launch_spmmv(h, X, ldx, Y, ldy, k, flags, s);
 
-    // host buffers: stage through device memory owned by the handle, in two
-    // slots used in turn.  A slot is reused only after its previous
+    // host buffers: stage through device memory owned by the handle, in
+    // kIoSlots slots used in turn.  A slot is reused only after its previous
     // device-to-host copy (event wait on this stream), and the products of
     // host-io calls run one after another whatever their streams (they share
     // the long-row scratch), so calls may alternate streams to overlap their
@@ -214,7 +244,7 @@ sell_status sell_spmmv(sell_handle h, const void *X, int64_t ldx, void *Y, int64
     if (sl.used) SELL_CUDA_TRY(cudaStreamWaitEvent(s, sl.done, 0));
     SELL_TRY(ensure_stage(h, &sl.x, &sl.xb, xb > 0 ? xb : 16, s));
     SELL_TRY(ensure_stage(h, &sl.y, &sl.yb, yb, s));
-    h->io_next ^= 1;
+    h->io_next = (h->io_next + 1) % sell_matrix::kIoSlots;
     const size_t row = (size_t)k * xs;
     if (xb) {
         if (ldx == k) SELL_CUDA_TRY(cudaMemcpyAsync(sl.x, X, xb, cudaMemcpyHostToDevice, s));
@@ -245,7 +275,8 @@ sell_status sell_spmv(sell_handle h, const void *x, void *y, uint32_t flags, voi
 sell_status sell_spmv_dot(sell_handle h, const void *x, void *y, uint32_t flags, double *dot, void *stream) {
     if (!h || !dot) return fail(SELL_EINVAL, "sell_spmv_dot: NULL argument");
     if (h->nrows != h->ncols) return fail(SELL_EINVAL, "sell_spmv_dot: the matrix must be square");
-    if (flags & SELL_SPMV_HOST_IO) return fail(SELL_EINVAL, "sell_spmv_dot: device vectors only");
+    if (flags & (SELL_SPMV_HOST_IO | SELL_SPMV_HOST_DIRECT))
+        return fail(SELL_EINVAL, "sell_spmv_dot: device vectors only");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     SELL_TRY(sell_spmmv(h, x, 1, y, 1, 1, flags, stream));
     if (h->nrows == 0) {

@@ -119,16 +119,21 @@ struct sell_matrix {
     mutable uint32_t expire_us = 0;  // one-shot test hook of sell_test_expire_wait (0: off),
                                      // consumed by the next bulk-staged launch
     double *dot_part = nullptr;  // range sums of sell_spmv_dot (lazily allocated)
-    // host-io staging (lazily allocated): two slots used in turn, so that the
-    // copies of one call overlap the kernel of the previous one when calls
-    // alternate streams.  done = recorded after the slot's last device-to-host
-    // copy; kdone = recorded after the latest host-io product's kernels.
+    // host-io staging (lazily allocated): kIoSlots slots used in turn, so that
+    // the copies of one call overlap the kernels of the previous ones when
+    // calls alternate streams.  A slot is reused only after its result has
+    // been copied out; with two slots that wait (the result copy of call i
+    // before the input copy of call i + 2) bounds a call at half of the two
+    // copies plus the kernel, with four the kernels set the pace.  done =
+    // recorded after the slot's last device-to-host copy; kdone = recorded
+    // after the latest host-io product's kernels.
+    static constexpr int kIoSlots = 4;
     struct IoSlot {
         void *x = nullptr, *y = nullptr;
         size_t xb = 0, yb = 0;
         cudaEvent_t done = nullptr;
         bool used = false;
-    } io[2];
+    } io[kIoSlots];
     int io_next = 0;
     cudaEvent_t kdone = nullptr;
     bool kdone_used = false;

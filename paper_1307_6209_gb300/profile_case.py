@@ -255,6 +255,20 @@ def run_copies():
     e2.record(sb)
     torch.cuda.synchronize()
     out["two_large_done_ms"] = [round(e0.elapsed_time(e1), 3), round(e0.elapsed_time(e2), 3)]
+    # a host-to-device and a device-to-host copy of 256 MB at once, on two streams
+    back_h = torch.empty_like(big_h).pin_memory()
+    torch.cuda.synchronize()
+    e0, e1, e2 = ev(), ev(), ev()
+    e0.record(sa)
+    sb.wait_event(e0)
+    with torch.cuda.stream(sa):
+        big_d.copy_(big_h, non_blocking=True)
+    with torch.cuda.stream(sb):
+        back_h.copy_(big_d2, non_blocking=True)
+    e1.record(sa)
+    e2.record(sb)
+    torch.cuda.synchronize()
+    out["h2d_and_d2h_done_ms"] = [round(e0.elapsed_time(e1), 3), round(e0.elapsed_time(e2), 3)]
     out["large_gbs"] = round(big_h.numel() * 8 / (out["trials"][-1]["large_done_ms"] * 1e-3) / 1e9, 1)
     print(json.dumps(out))
     return 0

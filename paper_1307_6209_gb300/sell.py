@@ -25,6 +25,7 @@ SELL_SPMV_ACCUMULATE = 0x1
 SELL_SPMV_COMPENSATED = 0x2
 SELL_SPMV_HOST_IO = 0x4
 SELL_SPMV_COMPENSATED_LONG = 0x8
+SELL_SPMV_HOST_DIRECT = 0x80
 SELL_SPMV_RHS_BLOCK4 = 0x10
 SELL_SPMV_RHS_BLOCK2 = 0x20
 SELL_SPMV_RHS_BLOCK1 = 0x40
@@ -261,7 +262,7 @@ def _check_vec(h: SellMatrix, t, name: str, host: bool, rows: bool = True):
         if not ok:
             raise TypeError(f"{name}: expected {'float64' if want64 else 'float32'}, got {t.dtype}")
         if not host:
-            raise TypeError(f"{name}: a numpy array needs SELL_SPMV_HOST_IO")
+            raise TypeError(f"{name}: a numpy array needs SELL_SPMV_HOST_IO or SELL_SPMV_HOST_DIRECT")
         inner = t.strides[-1] // t.itemsize if t.ndim > 1 else 1
     else:
         import torch
@@ -275,7 +276,7 @@ def _check_vec(h: SellMatrix, t, name: str, host: bool, rows: bool = True):
 
 
 def sell_spmv(h: SellMatrix, x, y, flags: int = 0, stream=None):
-    host = bool(int(flags) & SELL_SPMV_HOST_IO)
+    host = bool(int(flags) & (SELL_SPMV_HOST_IO | SELL_SPMV_HOST_DIRECT))
     _check_vec(h, x, "x", host)
     _check_vec(h, y, "y", host)
     _check(load().sell_spmv(h.handle, _ptr(x), _ptr(y), int(flags), _stream_ptr(stream)))
@@ -290,7 +291,7 @@ def sell_spmv_dot(h: SellMatrix, x, y, dot, flags: int = 0, stream=None):
 
 def sell_spmmv(h: SellMatrix, X, Y, flags: int = 0, stream=None, ldx=None, ldy=None, k=None):
     """Y = A X for row-major X (ncols x k) and Y (nrows x k)."""
-    host = bool(int(flags) & SELL_SPMV_HOST_IO)
+    host = bool(int(flags) & (SELL_SPMV_HOST_IO | SELL_SPMV_HOST_DIRECT))
     _check_vec(h, X, "X", host)
     _check_vec(h, Y, "Y", host)
     k = int(X.shape[1]) if k is None else int(k)

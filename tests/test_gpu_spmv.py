@@ -138,6 +138,49 @@ def test_spmmv_host_io_leading_dimensions(k, accumulate):
     assert np.ascontiguousarray(got[:, :k]).tobytes() == Yd.cpu().numpy().tobytes()
 
 
+@pytest.mark.parametrize("k", [1, 4])
+@pytest.mark.parametrize("accumulate", [False, True])
+def test_spmmv_host_direct(k, accumulate):
+    """HOST_DIRECT: the kernels read X from and write Y to page-locked host
+    memory in place (padded rows, ld = k + 3): the padding keeps the caller's
+    values, every column matches the oracle, and the result is the device
+    product bit for bit.  Pageable host memory is refused."""
+    import torch
+    from paper_1307_6209_gb300 import sell
+
+    A = synth.lognormal(6007, seed=50 + k, cap=900)
+    h = sell.sell_build(A, C=64, sigma=1024)
+    ld = k + 3
+    X = synth.block(A.ncols, k, seed=17)
+    Y0 = synth.block(A.nrows, k, seed=18)
+    Xh = torch.full((A.ncols, ld), 5.0, dtype=torch.float64).pin_memory()
+    Xh[:, :k] = torch.from_numpy(X)
+    Yh = torch.full((A.nrows, ld), -2.5, dtype=torch.float64).pin_memory()
+    if accumulate:
+        Yh[:, :k] = torch.from_numpy(Y0)
+    fl = sell.SELL_SPMV_HOST_DIRECT | (sell.SELL_SPMV_ACCUMULATE if accumulate else 0)
+    sell.sell_spmmv(h, Xh[:, :k], Yh[:, :k], flags=fl)
+    torch.cuda.synchronize()
+    got = Yh.numpy()
+    assert np.all(got[:, k:] == -2.5), "padding columns of Y were written"
+    ref = oracle.csr_spmmv(A, X, Y0=Y0 if accumulate else None, accumulate=accumulate)
+    rl = A.row_lengths()
+    for c in range(k):
+        scale = oracle.csr_absdot(A, X[:, c]) + (np.abs(Y0[:, c]) if accumulate else 0.0)
+        assert np.all(np.abs(got[:, c] - ref[:, c]) <= tol_f64(rl + (1 if accumulate else 0), scale)), f"col {c}"
+    Yd = torch.from_numpy(Y0).cuda() if accumulate else torch.empty((A.nrows, k), dtype=torch.float64,
+                                                                     device="cuda")
+    sell.sell_spmmv(h, torch.from_numpy(X).cuda(), Yd, flags=fl & ~sell.SELL_SPMV_HOST_DIRECT)
+    torch.cuda.synchronize()
+    assert np.ascontiguousarray(got[:, :k]).tobytes() == Yd.cpu().numpy().tobytes()
+    lib = sell.load()
+    xp, yp = np.ones(A.ncols), np.zeros(A.nrows)  # pageable
+    assert lib.sell_spmmv(h.handle, xp.ctypes.data, 1, yp.ctypes.data, 1, 1, sell.SELL_SPMV_HOST_DIRECT,
+                          None) == sell.SELL_EINVAL
+    assert lib.sell_spmmv(h.handle, xp.ctypes.data, 1, yp.ctypes.data, 1, 1,
+                          sell.SELL_SPMV_HOST_DIRECT | sell.SELL_SPMV_HOST_IO, None) == sell.SELL_EINVAL
+
+
 def test_spmv_host_io_alternating_streams():
     """HOST_IO calls that alternate two streams (the overlapped end-to-end
     pattern): every call's y is bitwise the device-buffer product of its own
