@@ -17,6 +17,10 @@
 //     fewest bytes left first; a batch's kernels are enqueued behind an event
 //     recorded after its last chunk.  A small request then waits for at
 //     most a window of chunks instead of a large request's whole input;
+//   * runs a batch in two parts when its products differ widely in size:
+//     the requests whose work is at most 1/kPartRatio of the batch's largest
+//     go first, with their own input copies, plan and completion event, so
+//     they complete without waiting for the large products of their batch;
 //   * keeps up to `streams` batches in flight, so requests that arrive while
 //     others run are admitted as soon as a stream and memory are free and
 //     their work overlaps on the device;
@@ -74,15 +78,27 @@ struct Chunk {
     size_t bytes;
 };
 
-struct Batch {
-    int si = 0;
+// A request is in the first part of its batch when its work is at most
+// 1/kPartRatio of the batch's largest request.
+constexpr double kPartRatio = 8.0;
+
+// One part of a batch: its requests, their input copies, its plan.
+struct Part {
     sell_batch *plan = nullptr;
     std::vector<Req *> reqs;
     std::vector<Chunk> chunks;  // its host-to-device copies, in order
     size_t next = 0;            // the next chunk to issue
     size_t left = 0;            // bytes not yet issued
     bool launched = false;      // kernels, result copies and completion event enqueued
+    bool retired = false;       // its requests are done
     sell_status status = SELL_OK;
+};
+
+// A batch holds one stream; its parts run on it in order (part 0 first).
+struct Batch {
+    int si = 0;
+    int nparts = 1;
+    Part parts[2];
 };
 
 bool is_pinned_host(const void *p) {
@@ -107,8 +123,8 @@ struct sell_server {
     char *arena_base = nullptr;
     sell::Arena arena;
     std::vector<cudaStream_t> streams;
-    std::vector<cudaEvent_t> events;  // one per stream (a stream holds at most one batch)
-    std::vector<cudaEvent_t> ready;   // one per stream: its batch's input copies issued (on h2d)
+    std::vector<cudaEvent_t> events;  // two per stream (a stream holds at most one batch): its parts done
+    std::vector<cudaEvent_t> ready;   // two per stream: each part's input copies issued (on h2d)
     cudaStream_t h2d = nullptr;       // the copy stream of every input
     std::deque<std::pair<cudaEvent_t, size_t>> copying;  // chunks in flight on h2d (event after each)
     std::vector<cudaEvent_t> spare;   // chunk events to reuse
@@ -179,45 +195,55 @@ void release_y(sell_server *S, Req *r) {
     r->reserved = false;
 }
 
-// Admit a batch on stream si: stamp its requests and list its input copies
-// in chunks (no CUDA call; the scheduler thread owns the batch from here).
+// Admit a batch on stream si: stamp its requests, split it into parts and
+// list each part's input copies in chunks (no CUDA call; the scheduler
+// thread owns the batch from here).
 void prepare(sell_server *S, int si, std::vector<Req *> &batch, Batch &B) {
     const double t = now_s();
     const int n = (int)batch.size();
     B.si = si;
-    B.reqs = batch;
-    auto add = [&](char *dst, const void *src, size_t bytes) {
-        const char *s = static_cast<const char *>(src);
-        for (size_t o = 0; o < bytes; o += kChunk) {
-            const size_t c = std::min(kChunk, bytes - o);
-            B.chunks.push_back({dst + o, s + o, c});
-            B.left += c;
-        }
-    };
+    double wmax = 0;
+    for (Req *r : batch) wmax = std::max(wmax, work(S, r));
+    int nsmall = 0;
+    for (Req *r : batch) nsmall += work(S, r) * kPartRatio <= wmax ? 1 : 0;
+    B.nparts = (nsmall > 0 && nsmall < n) ? 2 : 1;
     for (int i = 0; i < n; ++i) {
         Req *r = batch[i];
         r->tl = t;
         r->batch = n;
+        const int p = (B.nparts == 2 && work(S, r) * kPartRatio > wmax) ? 1 : 0;
+        Part &P = B.parts[p];
+        P.reqs.push_back(r);
+        auto add = [&](char *dst, const void *src, size_t bytes) {
+            const char *s = static_cast<const char *>(src);
+            for (size_t o = 0; o < bytes; o += kChunk) {
+                const size_t c = std::min(kChunk, bytes - o);
+                P.chunks.push_back({dst + o, s + o, c});
+                P.left += c;
+            }
+        };
         if (r->xb) add(S->arena_base + r->xoff, r->X, r->xb);
         if ((r->flags & SELL_SPMV_ACCUMULATE) && r->yb) add(S->arena_base + r->yoff, r->Y, r->yb);
     }
 }
 
-// Enqueue a batch whose input copies have all been issued: its stream waits
-// for them, then runs the plan, the result copies and the completion event
-// (called without the lock).
-void finish_launch(sell_server *S, Batch &B) {
+// Enqueue a part whose input copies have all been issued: its stream waits
+// for them, then runs the part's plan, its result copies and its completion
+// event (called without the lock).
+void finish_launch(sell_server *S, Batch &B, int p) {
+    Part &P = B.parts[p];
     const int si = B.si;
     cudaStream_t st = S->streams[si];
-    const int n = (int)B.reqs.size();
-    sell_status status = B.status;
-    if (status == SELL_OK && !B.chunks.empty() &&
-        (cudaEventRecord(S->ready[si], S->h2d) != cudaSuccess || cudaStreamWaitEvent(st, S->ready[si], 0) != cudaSuccess))
+    cudaEvent_t ready = S->ready[2 * si + p], done = S->events[2 * si + p];
+    const int n = (int)P.reqs.size();
+    sell_status status = P.status;
+    if (status == SELL_OK && !P.chunks.empty() &&
+        (cudaEventRecord(ready, S->h2d) != cudaSuccess || cudaStreamWaitEvent(st, ready, 0) != cudaSuccess))
         status = cuda_fail(cudaGetLastError(), "server: input copy ordering");
     std::vector<sell_batch_item> items(n);
     std::vector<void *> scr(n, nullptr);
     for (int i = 0; i < n; ++i) {
-        Req *r = B.reqs[i];
+        Req *r = P.reqs[i];
         items[i].A = S->mats[r->mid];
         items[i].X = S->arena_base + r->xoff;
         items[i].Y = S->arena_base + r->yoff;
@@ -228,48 +254,53 @@ void finish_launch(sell_server *S, Batch &B) {
         scr[i] = r->sb ? S->arena_base + r->soff : nullptr;
     }
     if (status == SELL_OK) {
-        B.plan = new (std::nothrow) sell_batch();
-        if (!B.plan) status = SELL_ENOMEM;
+        P.plan = new (std::nothrow) sell_batch();
+        if (!P.plan) status = SELL_ENOMEM;
     }
-    if (status == SELL_OK) status = batch_create(items.data(), n, st, B.plan, scr.data());
-    if (status == SELL_OK) status = batch_run(B.plan, 0, st);
+    if (status == SELL_OK) status = batch_create(items.data(), n, st, P.plan, scr.data());
+    if (status == SELL_OK) status = batch_run(P.plan, 0, st);
     for (int i = 0; i < n && status == SELL_OK; ++i) {
-        Req *r = B.reqs[i];
+        Req *r = P.reqs[i];
         if (!r->keep_y() && r->yb &&
             cudaMemcpyAsync(r->Y, S->arena_base + r->yoff, r->yb, cudaMemcpyDeviceToHost, st) != cudaSuccess)
             status = cuda_fail(cudaGetLastError(), "server: result copy");
     }
     if (status != SELL_OK)
-        for (Req *r : B.reqs) r->status = status;
-    if (cudaEventRecord(S->events[si], st) != cudaSuccess) {
+        for (Req *r : P.reqs) r->status = status;
+    if (cudaEventRecord(done, st) != cudaSuccess) {
         (void)cudaGetLastError();
         (void)cudaStreamSynchronize(st);
     }
-    B.launched = true;
+    P.launched = true;
 }
 
 // Feed the copy stream (called without the lock, scheduler thread only):
-// retire the chunks that have landed, launch the batches whose copies are
-// all issued, and issue further chunks while the window has room -- always
-// from the batch with the fewest bytes left (the earliest admitted on ties).
+// retire the chunks that have landed, launch the parts whose copies are all
+// issued (a batch's second part after its first), and issue further chunks
+// while the window has room -- always from the part with the fewest bytes
+// left (the earliest admitted on ties).
 void pump(sell_server *S) {
     while (!S->copying.empty()) {
         const cudaError_t q = cudaEventQuery(S->copying.front().first);
         if (q == cudaErrorNotReady) break;
-        if (q != cudaSuccess) (void)cudaGetLastError();  // the batch's own event reports the failure
+        if (q != cudaSuccess) (void)cudaGetLastError();  // the part's own event reports the failure
         S->copy_bytes -= S->copying.front().second;
         S->spare.push_back(S->copying.front().first);
         S->copying.pop_front();
     }
     for (;;) {
-        Batch *pick = nullptr;
+        Part *pick = nullptr;
         for (Batch &B : S->inflight) {
-            if (B.launched) continue;
-            if (B.next == B.chunks.size()) {
-                finish_launch(S, B);
-                continue;
+            for (int p = 0; p < B.nparts; ++p) {
+                Part &P = B.parts[p];
+                if (P.launched) continue;
+                if (p > 0 && !B.parts[p - 1].launched) break;  // parts launch in order
+                if (P.next == P.chunks.size()) {
+                    finish_launch(S, B, p);
+                    continue;
+                }
+                if (!pick || P.left < pick->left) pick = &P;
             }
-            if (!pick || B.left < pick->left) pick = &B;
         }
         if (!pick || S->copy_bytes >= kWindow) return;
         const Chunk &c = pick->chunks[pick->next];
@@ -284,7 +315,7 @@ void pump(sell_server *S) {
             cudaEventRecord(ev, S->h2d) != cudaSuccess) {
             pick->status = cuda_fail(cudaGetLastError(), "server: input copy");
             if (ev) S->spare.push_back(ev);
-            pick->next = pick->chunks.size();  // no further copies; the batch reports the failure
+            pick->next = pick->chunks.size();  // no further copies; the part reports the failure
             pick->left = 0;
             continue;
         }
@@ -303,32 +334,43 @@ void scheduler(sell_server *S) {
         bool retired = false;
         for (size_t i = 0; i < S->inflight.size();) {
             Batch &B = S->inflight[i];
-            if (!B.launched) {  // still waiting for its input copies
+            bool all = true;
+            for (int p = 0; p < B.nparts; ++p) {
+                Part &P = B.parts[p];
+                if (P.retired) continue;
+                if (!P.launched) {  // still waiting for its input copies
+                    all = false;
+                    continue;
+                }
+                const cudaError_t q = cudaEventQuery(S->events[2 * B.si + p]);
+                if (q == cudaErrorNotReady) {
+                    all = false;
+                    continue;
+                }
+                if (q != cudaSuccess) (void)cudaGetLastError();
+                const double t = now_s();
+                for (Req *r : P.reqs) {
+                    r->td = t;
+                    if (q != cudaSuccess && r->status == SELL_OK) r->status = SELL_ECUDA;
+                    release_x_s(S, r);
+                    if (!r->keep_y() || r->status != SELL_OK) release_y(S, r);
+                    r->state = kDone;
+                    S->completed.push_back(r->id);
+                }
+                if (P.plan) {
+                    batch_release(P.plan, S->streams[B.si]);
+                    delete P.plan;
+                    P.plan = nullptr;
+                }
+                P.retired = true;
+                retired = true;
+            }
+            if (!all) {
                 ++i;
                 continue;
-            }
-            const cudaError_t q = cudaEventQuery(S->events[B.si]);
-            if (q == cudaErrorNotReady) {
-                ++i;
-                continue;
-            }
-            if (q != cudaSuccess) (void)cudaGetLastError();
-            const double t = now_s();
-            for (Req *r : B.reqs) {
-                r->td = t;
-                if (q != cudaSuccess && r->status == SELL_OK) r->status = SELL_ECUDA;
-                release_x_s(S, r);
-                if (!r->keep_y() || r->status != SELL_OK) release_y(S, r);
-                r->state = kDone;
-                S->completed.push_back(r->id);
-            }
-            if (B.plan) {
-                batch_release(B.plan, S->streams[B.si]);
-                delete B.plan;
             }
             S->free_streams.push_back(B.si);
             S->inflight.erase(S->inflight.begin() + i);
-            retired = true;
         }
         if (retired) S->cv_done.notify_all();
         // admit in arrival order while the footprint fits, then launch.  With
@@ -474,14 +516,17 @@ sell_status sell_server_create(const sell_handle *mats, int32_t n, const sell_se
     sell_status st = SELL_OK;
     for (int i = 0; i < S->nstreams && st == SELL_OK; ++i) {
         cudaStream_t s = nullptr;
-        cudaEvent_t e = nullptr, rd = nullptr;
-        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&rd, cudaEventDisableTiming) != cudaSuccess)
-            st = cuda_fail(cudaGetLastError(), "sell_server_create: stream/event");
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
+            st = cuda_fail(cudaGetLastError(), "sell_server_create: stream");
         S->streams.push_back(s);
-        S->events.push_back(e);
-        S->ready.push_back(rd);
+        for (int p = 0; p < 2 && st == SELL_OK; ++p) {
+            cudaEvent_t e = nullptr, rd = nullptr;
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&rd, cudaEventDisableTiming) != cudaSuccess)
+                st = cuda_fail(cudaGetLastError(), "sell_server_create: event");
+            S->events.push_back(e);
+            S->ready.push_back(rd);
+        }
         S->free_streams.push_back(i);
     }
     if (st == SELL_OK && cudaStreamCreateWithFlags(&S->h2d, cudaStreamNonBlocking) != cudaSuccess)

@@ -318,3 +318,39 @@ def test_small_inputs_are_copied_ahead_of_a_large_one():
     for r in small:
         assert r.Y.numpy().tobytes() == _alone(mats[0], r.X).numpy().tobytes()
         assert_oracle_parity(hosts[0], mats[0].info.store_type, r.X.numpy(), r.Y.numpy(), what=f"request {r.rid}")
+
+
+def test_small_requests_of_a_mixed_batch_complete_first():
+    """A batch that mixes small and large products runs in two parts on its
+    stream, the small products first with their own completion event: small
+    requests admitted together with a large one complete before it.  Every
+    result is the request alone, and the oracle's product within its bound."""
+    import torch
+    from paper_1307_6209_gb300 import serving, sell
+    Abig = synth.lognormal_device(2_000_000, seed=17)
+    big = sell.sell_build(Abig, C=32, sigma=2_000_000)
+    hosts = []
+    mats = _mats(seed=95, hosts=hosts) + [big]
+    hosts.append(host_csr(Abig))
+    del Abig
+    # one stream: the first large request runs alone; the next ones queue
+    # meanwhile and are admitted together as one mixed batch
+    srv = serving.Server(mats, hbm_budget_bytes=sum(m.info.device_bytes for m in mats) + (4 << 30), max_batch=16,
+                         streams=1)
+    Xb = [torch.rand((big.info.ncols, 8), dtype=torch.float64).pin_memory() for _ in range(2)]
+    small_x = [torch.rand((mats[0].info.ncols, 2), dtype=torch.float64).pin_memory() for _ in range(4)]
+    first = srv.submit(len(mats) - 1, Xb[0], to_host=True)
+    large = srv.submit(len(mats) - 1, Xb[1], to_host=True)
+    small = [srv.submit(0, x, to_host=True) for x in small_x]
+    for r in [first, large] + small:
+        r.wait(60)
+    srv.stop()
+    mixed = [r for r in small if r.t_launch == large.t_launch]
+    assert mixed, "no small request shared the large one's batch"
+    assert max(r.t_done for r in mixed) < large.t_done, "the small part did not complete first"
+    for r in [first, large]:
+        assert r.Y.numpy().tobytes() == _alone(big, r.X).numpy().tobytes()
+    assert_oracle_parity(hosts[-1], sell.SELL_F64, large.X.numpy(), large.Y.numpy(), what="large request")
+    for r in small:
+        assert r.Y.numpy().tobytes() == _alone(mats[0], r.X).numpy().tobytes()
+        assert_oracle_parity(hosts[0], mats[0].info.store_type, r.X.numpy(), r.Y.numpy(), what=f"request {r.rid}")
