@@ -843,16 +843,23 @@ def serving_section(sell, stream, nmat=64, seed=0, duration_s=1.5, repeats=3):
            "nnz_total": int(sum(h.info.nnz for h in mats)),
            "small_request_work": small_work,
            "size_classes": "small: stored elements x k at most the median request's; large: the rest"}
-    # warm-up (kernels, arena, pinned memory), then the saturated rate from a burst
+    # warm-up (kernels, arena, pinned memory), then the saturated rate: the
+    # median of three bursts of 400 requests (one burst varies by 2x from
+    # process to process)
     srv = serving.Server(mats, budget, max_batch=64, streams=6)
     serving.burst_load(srv, 200, make, seed=1, to_host=False)
     srv.stop()
-    srv = serving.Server(mats, budget, max_batch=64, streams=6)
-    burst, dt = serving.burst_load(srv, 400, make, seed=2, to_host=False)
-    sat = len(burst) / dt
+    sats = []
+    for sd in (2, 3, 4):
+        srv = serving.Server(mats, budget, max_batch=64, streams=6)
+        burst, dt = serving.burst_load(srv, 400, make, seed=sd, to_host=False)
+        sats.append(len(burst) / dt)
+        if sd == 2:
+            out["burst"] = rnd(srv.stats(split_work=small_work))
+        srv.stop()
+    sat = statistics.median(sats)
     out["saturated_req_per_s"] = round(sat, 1)
-    out["burst"] = rnd(srv.stats(split_work=small_work))
-    srv.stop()
+    out["saturated_runs"] = [round(v, 1) for v in sats]
     for frac in (0.5, 0.8, 0.95):
         runs = [one_load(frac * sat, 7 + rep) for rep in range(repeats)]
         row = rnd(runs[0])
