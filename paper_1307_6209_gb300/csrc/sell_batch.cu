@@ -139,15 +139,16 @@ __global__ void __launch_bounds__(kTileRows, 4) k_batch_wide(const __grid_consta
 }
 
 // Products without long rows (every row at most kSeg entries) at one right-
-// hand side get an entry point with the long-row path compiled out, which
-// fits in 32 registers without spills: 8 resident blocks of 256 threads, every
-// warp slot of the SM.  Measured on the 256 banded matrices of the benchmark
-// batch (binary32): 0.766 -> 0.837 of the HBM copy bandwidth.  (Capping the
-// kernel with the long-row path at 32 registers instead spills 96-112 bytes
-// and made the mixed 512-matrix batch 1 % slower.)
+// hand side get an entry point of their own, capped at 32 registers: 8
+// resident blocks of 256 threads, every warp slot of the SM.  ptxas places
+// its spills (96-112 bytes) in the long-row path, which these products never
+// enter.  Measured on the 256 banded matrices of the benchmark batch
+// (binary32): 0.766 -> 0.837 of the HBM copy bandwidth.  (The same cap on
+// the products with long rows made the mixed 512-matrix batch 1 % slower;
+// an entry point with the long-row path compiled out reached only 0.807.)
 template <class VT, class Acc>
 __global__ void __launch_bounds__(kTileRows, 8) k_batch_short(const __grid_constant__ LaunchParams lp) {
-    batch_unit<VT, 1, Acc, Acc, false>(lp);
+    batch_unit<VT, 1, Acc, Acc, true>(lp);
 }
 
 using KernelFn = void (*)(const LaunchParams);
