@@ -362,11 +362,16 @@ SELL_API sell_status sell_batch_free(sell_batch_plan plan);
  * footprint -- the x block, the y block and the long-row scratch -- fits in
  * an arena of budget - resident bytes (allocated once at creation, so the
  * budget is never exceeded), packs the admitted ones into one batch plan
- * (sell_batch_create) on a free stream with the host-to-device copies before
- * it and the device-to-host copies after it, and keeps up to `streams`
- * batches in flight: requests that arrive while others run are admitted as
- * soon as a stream and memory are free, and their work overlaps on the
- * device.  Every result is bitwise the result of the same product alone. */
+ * (sell_batch_create) on a free stream with the device-to-host copies after
+ * it, and keeps up to `streams` batches in flight: requests that arrive while
+ * others run are admitted as soon as a stream and memory are free, and their
+ * work overlaps on the device.  The inputs of all batches go through one
+ * copy stream of the server's in 4 MB pieces, the batch with the fewest bytes
+ * left first, so a small request's input does not wait for a large one's;
+ * a batch's kernels start once its inputs are issued.  A batch whose requests
+ * differ widely in size runs in two parts, the small requests (work at most
+ * 1/8 of its largest) first with their own completion.  Every result is
+ * bitwise the result of the same product alone. */
 typedef struct sell_server *sell_server_t;
 
 typedef struct {
