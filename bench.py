@@ -138,8 +138,10 @@ def kernel_name(best, C, inf):
         ring = {1: 1, 2: 2, 4: 3, 8: 4}[best.unroll]
         return (f"k_spmv_bulk<double,Plain<double>,{C // 32},{long_rows}> {best.block // 32} warps/block, "
                 f"{ring} pieces per warp")
-    return (f"k_spmmv<double,1,{best.unroll},{'true' if best.pipeline else 'false'},Plain<double>,{long_rows}> "
-            f"block {best.block}")
+    pipe = 'true' if best.pipeline else 'false'
+    if long_rows == "false":  # one vector without long rows: the full-occupancy entry point
+        return f"k_spmv_short<double,{best.unroll},{pipe},Plain<double>> block {best.block}"
+    return f"k_spmmv<double,1,{best.unroll},{pipe},Plain<double>,true> block {best.block}"
 
 
 def lookup_traffic(workload_key):

@@ -32,8 +32,8 @@ namespace spmv_impl {
 // AccL: the accumulation of the long rows' segments (Acc unless only long
 // rows are compensated, SELL_SPMV_COMPENSATED_LONG).
 template <class VT, int K, int U, bool PIPE, class Acc, bool LONG, class AccL = Acc>
-__global__ void __launch_bounds__(512)
-k_spmmv(const VT *__restrict__ val, const int32_t *__restrict__ col, const int64_t *__restrict__ cs,
+__device__ __forceinline__ void spmmv_body(
+        const VT *__restrict__ val, const int32_t *__restrict__ col, const int64_t *__restrict__ cs,
         const int32_t *__restrict__ srl, const int32_t *__restrict__ perm, const int32_t *__restrict__ lchunk,
         const int2 *__restrict__ lunit, const int4 *__restrict__ lmeta, const int32_t *__restrict__ lrow,
         int64_t long_threads, int64_t long_blocks, AccL *part, int32_t *cnt,
@@ -56,6 +56,39 @@ k_spmmv(const VT *__restrict__ val, const int32_t *__restrict__ col, const int64
     short_row<VT, XT, K, U, PIPE, Acc>(val, col, cs, srl, perm, X, ldx, Y, ldy, C, r, accumulate, vec != 0, pol);
 }
 
+#define SELL_SPMMV_PARAMS                                                                                        \
+    const VT *__restrict__ val, const int32_t *__restrict__ col, const int64_t *__restrict__ cs,               \
+        const int32_t *__restrict__ srl, const int32_t *__restrict__ perm, const int32_t *__restrict__ lchunk, \
+        const int2 *__restrict__ lunit, const int4 *__restrict__ lmeta, const int32_t *__restrict__ lrow,      \
+        int64_t long_threads, int64_t long_blocks, AccL *part, int32_t *cnt, int32_t *cnt2,                    \
+        const typename XType<VT>::T *__restrict__ X, int64_t ldx, typename XType<VT>::T *Y, int64_t ldy,      \
+        int64_t N, int C, int accumulate, int vec
+#define SELL_SPMMV_ARGS                                                                                 \
+    val, col, cs, srl, perm, lchunk, lunit, lmeta, lrow, long_threads, long_blocks, part, cnt, cnt2, X, ldx, \
+        Y, ldy, N, C, accumulate, vec
+
+template <class VT, int K, int U, bool PIPE, class Acc, bool LONG, class AccL = Acc>
+__global__ void __launch_bounds__(512) k_spmmv(SELL_SPMMV_PARAMS) {
+    spmmv_body<VT, K, U, PIPE, Acc, LONG, AccL>(SELL_SPMMV_ARGS);
+}
+
+// Occupancy: the one-vector kernel of matrices without long rows asks for 4
+// resident blocks of 512 threads, i.e. 32 registers -- every warp slot of
+// the SM at any block size.  Its pipelined forms would otherwise take 39-40
+// registers (48 of 64 warps); capped they spill 12-28 bytes and still run
+// faster, measured on the 200^3 stencil: binary64 (unroll 2, pipelined)
+// 467 -> 420 us, the best launch overall (425.5 us before); binary32
+// (unroll 4, pipelined) 319 -> 295 us; bfloat16 unchanged.  The other
+// kernels keep the allocation ptxas picks (capping the wider ones spills
+// hundreds of bytes).
+template <class VT, int U, bool PIPE, class Acc, class AccL = Acc>
+__global__ void __launch_bounds__(512, 4) k_spmv_short(SELL_SPMMV_PARAMS) {
+    spmmv_body<VT, 1, U, PIPE, Acc, false, AccL>(SELL_SPMMV_ARGS);
+}
+
+#undef SELL_SPMMV_PARAMS
+#undef SELL_SPMMV_ARGS
+
 // One launch of k_spmmv with the given long-row scratch (the handle's own,
 // or the caller's for sell_spmmv_noalloc).
 template <class VT, int K, int U, bool PIPE, class Acc, class AccL = Acc>
@@ -66,8 +99,15 @@ cudaError_t run_with(const sell_matrix *h, const void *X, int64_t ldx, void *Y, 
     const int64_t long_blocks = (long_threads + h->block - 1) / h->block;
     const int64_t grid = long_blocks + (h->nrows + h->block - 1) / h->block;
     // without long rows the long-row path is compiled out, so that it does
-    // not cost the per-row path registers or scheduling freedom
-    auto kern = h->nunits ? k_spmmv<VT, K, U, PIPE, Acc, true, AccL> : k_spmmv<VT, K, U, PIPE, Acc, false, AccL>;
+    // not cost the per-row path registers or scheduling freedom; one vector
+    // without long rows runs at full occupancy (k_spmv_short)
+    auto pick = [&]() {
+        if constexpr (K == 1)
+            return h->nunits ? k_spmmv<VT, 1, U, PIPE, Acc, true, AccL> : k_spmv_short<VT, U, PIPE, Acc, AccL>;
+        else
+            return h->nunits ? k_spmmv<VT, K, U, PIPE, Acc, true, AccL> : k_spmmv<VT, K, U, PIPE, Acc, false, AccL>;
+    };
+    auto kern = pick();
     kern<<<(unsigned)grid, h->block, 0, s>>>(
         static_cast<const VT *>(h->val), h->col, h->cs, h->srl,
         (h->flags & SELL_BUILD_PERMUTE_COLS) ? nullptr : h->perm, h->lchunk, h->lunit, h->lmeta, h->lrow,
