@@ -96,14 +96,14 @@ __device__ __forceinline__ void batch_unit(const LaunchParams &lp) {
             long_unit<VT, XT, K, U, PIPE, AccL>(static_cast<const VT *>(P.val), P.col, P.cs, P.srl, P.perm,
                                          P.lchunk, P.lunit, P.lmeta, P.lrow, static_cast<AccL *>(P.part), P.cnt, P.cnt2,
                                          static_cast<const XT *>(P.X),
-                                         P.ldx, static_cast<XT *>(P.Y), P.ldy, P.N, P.C, v, P.acc, P.vec != 0, pol);
+                                         P.ldx, static_cast<XT *>(P.Y), P.ldy, P.N, P.C, v, P.acc, P.vec, pol);
         return;
     }
     const int64_t r = first + threadIdx.x;
     if (r < P.N)
         short_row<VT, XT, K, U, PIPE, Acc>(static_cast<const VT *>(P.val), P.col, P.cs, P.srl, P.perm,
                                      static_cast<const XT *>(P.X), P.ldx, static_cast<XT *>(P.Y), P.ldy, P.C, r, P.acc,
-                                     P.vec != 0, pol);
+                                     P.vec, pol);
 }
 
 // The kernel holds both the long-row path (segment folds) and the short-row
@@ -304,7 +304,7 @@ sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s
             P.type = h->store_type;
             P.acc = (it.flags & SELL_SPMV_ACCUMULATE) ? 1 : 0;
             P.comp = h->store_type != SELL_F64 ? comp_mode(it.flags) : 0;
-            P.vec = (((uintptr_t)P.X % 16) == 0 && ((it.ldx * xs) % 16) == 0) ? 1 : 0;
+            P.vec = x_vec(P.X, it.ldx, xs);
             prods.push_back(P);
             owner.push_back(h);
             done += kb;

@@ -82,6 +82,15 @@ inline int rhs_block(int rem, int maxw) {
     return kb;
 }
 
+// How the kernels may load a row of X (base X, row pitch ldx elements of xs
+// bytes): 2 with 32-byte vectors, 1 with 16-byte vectors, 0 value by value.
+inline int x_vec(const void *X, int64_t ldx, size_t xs) {
+    const uintptr_t a = (uintptr_t)X;
+    const int64_t pitch = ldx * (int64_t)xs;
+    if (a % 32 == 0 && pitch % 32 == 0) return 2;
+    return (a % 16 == 0 && pitch % 16 == 0) ? 1 : 0;
+}
+
 }  // namespace sell
 
 // ------------------------------------------------------------------ handle

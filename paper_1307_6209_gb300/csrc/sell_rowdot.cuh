@@ -107,16 +107,35 @@ struct PartOf<Plain<float>> {
     }
 };
 
+// 32 bytes of x at p (32-byte aligned) in one 256-bit load (sm_100 and later).
+__device__ __forceinline__ void ld_x32(const float *p, float *v) {
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+        : "l"(p));
+}
+__device__ __forceinline__ void ld_x32(const double *p, double *v) {
+    asm("ld.global.nc.v4.f64 {%0,%1,%2,%3}, [%4];" : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3]) : "l"(p));
+}
+
 // K consecutive right-hand-side values of row `ci` of X (row-major, ldx).
+// vec: 2 when X and its row pitch are 32-byte aligned (rows of a multiple of
+// 32 bytes then take one 256-bit load per 32 bytes: a random row costs one
+// L1 request instead of two), 1 when they are 16-byte aligned (16-byte
+// vector loads), 0 otherwise (one load per value).  The values loaded are
+// the same in every case.
 template <int K, class XT>
-__device__ __forceinline__ void load_x(const XT *__restrict__ X, int64_t ldx, int32_t ci, bool vec,
+__device__ __forceinline__ void load_x(const XT *__restrict__ X, int64_t ldx, int32_t ci, int vec,
                                        XT (&xv)[K]) {
     const XT *p = X + (int64_t)ci * ldx;
     if constexpr (K == 1) {
         xv[0] = __ldg(p);
     } else {
         constexpr int V = 16 / sizeof(XT);  // elements per 16-byte vector
-        if ((K % V) == 0 && vec) {
+        constexpr int W = 32 / sizeof(XT);  // elements per 32-byte vector
+        if ((K % W) == 0 && vec >= 2) {
+#pragma unroll
+            for (int q = 0; q < K; q += W) ld_x32(p + q, xv + q);
+        } else if ((K % V) == 0 && vec) {
             if constexpr (sizeof(XT) == 8) {
 #pragma unroll
                 for (int q = 0; q < K; q += 2) {
@@ -151,7 +170,7 @@ __device__ __forceinline__ void load_x(const XT *__restrict__ X, int64_t ldx, in
 template <class VT, class XT, int K, int U, bool PIPE, class Acc>
 __device__ __forceinline__ void chain(Acc (&acc)[K], const VT *__restrict__ vp,
                                       const int32_t *__restrict__ cp, int C, int j0, int j1,
-                                      const XT *__restrict__ X, int64_t ldx, bool vec, uint64_t pol) {
+                                      const XT *__restrict__ X, int64_t ldx, int vec, uint64_t pol) {
     const int64_t stride = C;
     vp += (int64_t)j0 * stride;
     cp += (int64_t)j0 * stride;
@@ -290,7 +309,7 @@ __device__ __forceinline__ void long_unit(const VT *__restrict__ val, const int3
                                           const int2 *__restrict__ lunit, const int4 *__restrict__ lmeta,
                                           const int32_t *__restrict__ lrow, Acc *part, int32_t *cnt,
                                           int32_t *cnt2, const XT *__restrict__ X, int64_t ldx, XT *Y,
-                                          int64_t ldy, int64_t N, int C, int64_t v, int accumulate, bool vec,
+                                          int64_t ldy, int64_t N, int C, int64_t v, int accumulate, int vec,
                                           uint64_t pol) {
     const int64_t u = v / C;
     const int t = (int)(v - u * C);
@@ -361,7 +380,7 @@ __device__ __forceinline__ void short_row(const VT *__restrict__ val, const int3
                                           const int64_t *__restrict__ cs, const int32_t *__restrict__ srl,
                                           const int32_t *__restrict__ perm, const XT *__restrict__ X,
                                           int64_t ldx, XT *Y, int64_t ldy, int C, int64_t r, int accumulate,
-                                          bool vec, uint64_t pol) {
+                                          int vec, uint64_t pol) {
     const int L = srl[r];
     if (L > kSeg) return;
     const int64_t c = r / C;

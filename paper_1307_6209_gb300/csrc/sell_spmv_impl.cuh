@@ -47,13 +47,13 @@ __device__ __forceinline__ void spmmv_body(
             const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
             if (v < long_threads)
                 long_unit<VT, XT, K, U, PIPE, AccL>(val, col, cs, srl, perm, lchunk, lunit, lmeta, lrow, part, cnt,
-                                                    cnt2, X, ldx, Y, ldy, N, C, v, accumulate, vec != 0, pol);
+                                                    cnt2, X, ldx, Y, ldy, N, C, v, accumulate, vec, pol);
             return;
         }
     }
     const int64_t r = (blockIdx.x - long_blocks) * (int64_t)blockDim.x + threadIdx.x;
     if (r >= N) return;
-    short_row<VT, XT, K, U, PIPE, Acc>(val, col, cs, srl, perm, X, ldx, Y, ldy, C, r, accumulate, vec != 0, pol);
+    short_row<VT, XT, K, U, PIPE, Acc>(val, col, cs, srl, perm, X, ldx, Y, ldy, C, r, accumulate, vec, pol);
 }
 
 #define SELL_SPMMV_PARAMS                                                                                        \

@@ -347,3 +347,40 @@ def test_spmmv_rhs_block_flags_keep_the_bits(k):
         sell.sell_spmmv(h, X, Y, flags=fl)
         torch.cuda.synchronize()
         assert torch.equal(Y, ref), f"flags {fl:#x}"
+
+
+@pytest.mark.parametrize("store,k", [("f64", 4), ("f64", 8), ("f32", 8), ("f32", 16)])
+def test_spmmv_x_row_load_widths_keep_the_bits(store, k):
+    """A row of X is loaded 32 bytes at a time when X and its pitch are
+    32-byte aligned, 16 bytes at a time when they are 16-byte aligned, value
+    by value otherwise.  The pitch (ldx = k, k + 16 / size, k + 1) and a
+    shifted base pick each width; every result is the same bits, within the
+    oracle's bound, through the batch plan as well."""
+    import torch
+    from paper_1307_6209_gb300 import sell
+    from tests.gpu_util import assert_oracle_parity
+
+    st = {"f64": sell.SELL_F64, "f32": sell.SELL_F32}[store]
+    dt = torch.float64 if store == "f64" else torch.float32
+    es = 8 if store == "f64" else 4
+    A = synth.lognormal(7000, seed=60 + k, cap=900)
+    h = sell.sell_build(A, C=64, sigma=4096, store_type=st)
+    X0 = torch.from_numpy(synth.block(A.ncols, k, seed=k)).to(dt)
+    ref = None
+    for ldx, shift in ((k, 0), (k + 16 // es, 0), (k + 1, 0), (k, 16 // es)):
+        buf = torch.full((A.ncols * ldx + shift + 64,), float("nan"), dtype=dt, device="cuda")
+        X = buf[shift:shift + A.ncols * ldx].view(A.ncols, ldx)[:, :k]
+        X.copy_(X0)
+        Y = torch.full((A.nrows, k), float("nan"), dtype=dt, device="cuda")
+        sell.sell_spmmv(h, X, Y)
+        torch.cuda.synchronize()
+        if ref is None:
+            ref = Y.clone()
+            assert_oracle_parity(A, st, X0.numpy(), Y.cpu().numpy(), what=f"{store} k={k}")
+        assert torch.equal(Y, ref), f"ldx {ldx}, base shift {shift}"
+        Yb = torch.full((A.nrows, k), float("nan"), dtype=dt, device="cuda")
+        plan = sell.sell_batch_create([(h, X, Yb, 0)])
+        plan.run()
+        torch.cuda.synchronize()
+        plan.free()
+        assert torch.equal(Yb, ref), f"batch: ldx {ldx}, base shift {shift}"
