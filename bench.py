@@ -261,8 +261,8 @@ class SmiClocks:
         for ln in self.proc.stdout:
             self.samples.append((time.perf_counter(), [v.strip() for v in ln.split(",")]))
 
-    def section(self, name, t0, t1):
-        self.sections.append((name, t0, t1))
+    def section(self, name, t0, t1, note=None):
+        self.sections.append((name, t0, t1, note))
 
     def stop(self):
         if self.proc:
@@ -271,6 +271,14 @@ class SmiClocks:
                 self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
+        self.proc = None
+
+    def pause(self):
+        """Stop sampling for a while (resume() starts a new nvidia-smi)."""
+        self.stop()
+
+    def resume(self):
+        return self.start()
 
     def summary(self, t0, t1):
         win = [s for t, s in self.samples if t0 <= t <= t1]
@@ -287,7 +295,12 @@ class SmiClocks:
                 "power_w_median": statistics.median(pw) if pw else None}
 
     def by_section(self):
-        return {name: self.summary(t0, t1) for name, t0, t1 in self.sections}
+        out = {}
+        for name, t0, t1, note in self.sections:
+            out[name] = self.summary(t0, t1)
+            if note:
+                out[name]["note"] = note
+        return out
 
 
 # ------------------------------------------------------------------ helpers
@@ -845,9 +858,10 @@ def serving_section(sell, stream, nmat=64, seed=0, duration_s=1.5, repeats=3):
            "nnz_total": int(sum(h.info.nnz for h in mats)),
            "small_request_work": small_work,
            "size_classes": "small: stored elements x k at most the median request's; large: the rest"}
-    # warm-up (kernels, arena, pinned memory), then the saturated rate: the
-    # median of three bursts of 400 requests (one burst varies by 2x from
-    # process to process)
+    # warm-up (kernels, arena, pinned memory); three bursts of 400 requests
+    # for context (one burst lasts ~50 ms, so a single stall halves its rate);
+    # then the saturated rate: completions per second in steady state, 256
+    # requests kept outstanding for 2 s
     srv = serving.Server(mats, budget, max_batch=64, streams=6)
     serving.burst_load(srv, 200, make, seed=1, to_host=False)
     srv.stop()
@@ -859,9 +873,15 @@ def serving_section(sell, stream, nmat=64, seed=0, duration_s=1.5, repeats=3):
         if sd == 2:
             out["burst"] = rnd(srv.stats(split_work=small_work))
         srv.stop()
-    sat = statistics.median(sats)
+    out["burst_req_per_s"] = [round(v, 1) for v in sats]
+    srv = serving.Server(mats, budget, max_batch=64, streams=6)
+    n_done, dt = serving.closed_loop(srv, 256, 2.0, make, seed=5, to_host=False)
+    st = srv.stats()
+    srv.stop()
+    sat = n_done / dt
     out["saturated_req_per_s"] = round(sat, 1)
-    out["saturated_runs"] = [round(v, 1) for v in sats]
+    out["saturated_how"] = "closed loop, 256 requests outstanding, 2 s"
+    out["saturated_mean_batch"] = round(st["mean_batch"], 2)
     for frac in (0.5, 0.8, 0.95):
         runs = [one_load(frac * sat, 7 + rep) for rep in range(repeats)]
         row = rnd(runs[0])
@@ -1224,6 +1244,13 @@ def run_ours(args):
             if W["name"] == "lognormal":
                 sections = sections[1:]
             for key, fn in sections:
+                # no clock sampler runs beside the serving loads: a process
+                # polling NVML stalls the server's completions every ~0.5 s
+                # (p99 at 0.8x load 80-130 ms with a 10 ms poller, 7-17 ms
+                # without, on one GPU in one run)
+                unsampled = key == "serving"
+                if unsampled:
+                    smi.pause()
                 t_sec = time.perf_counter()
                 try:
                     extras[key] = fn()
@@ -1231,7 +1258,10 @@ def run_ours(args):
                     extras[key] = {"error": f"{type(e).__name__}: {e}"}
                     torch.cuda.synchronize()
                     torch.cuda.empty_cache()
-                smi.section(key, t_sec, time.perf_counter())
+                smi.section(key, t_sec, time.perf_counter(),
+                            note="sampler paused: NVML polling stalls the server" if unsampled else None)
+                if unsampled:
+                    smi.resume()
 
     # ---- roofline of the dominant kernel (the SpMV)
     alg = model.algorithmic_bytes(nrows, ncols, nnz, inf.nchunks, C, 8, 8, inf.has_perm)

@@ -302,3 +302,37 @@ def _poisson_load(server, rate_hz, duration_s, make_request, seed, to_host):
         c.put(r)
     c.finish()
     return reqs
+
+
+def closed_loop(server: Server, outstanding: int, duration_s: float, make_request, seed: int = 0,
+                to_host: bool = True):
+    """Saturated throughput in steady state: keep `outstanding` requests
+    queued or running for duration_s (each completion submits the next
+    request), then drain.  Returns (requests completed within the window,
+    window seconds); the caller divides."""
+    with _NoGC():
+        return _closed_loop(server, outstanding, duration_s, make_request, seed, to_host)
+
+
+def _closed_loop(server, outstanding, duration_s, make_request, seed, to_host):
+    rng = np.random.default_rng(seed)
+    live = 0
+    for _ in range(outstanding):
+        server.submit(*make_request(rng), to_host=to_host)
+        live += 1
+    t0 = time.perf_counter()
+    done = 0
+    while True:
+        r = server.next(60.0)
+        r.release()
+        live -= 1
+        if time.perf_counter() - t0 >= duration_s:
+            break
+        done += 1
+        server.submit(*make_request(rng), to_host=to_host)
+        live += 1
+    t1 = time.perf_counter()
+    while live > 0:
+        server.next(60.0).release()
+        live -= 1
+    return done, t1 - t0

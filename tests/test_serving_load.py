@@ -70,3 +70,43 @@ def test_burst_load_submits_all_and_collects_all():
     reqs, secs = serving.burst_load(srv, 500, _make, seed=1)
     assert len(reqs) == 500 and all(r.released for r in reqs) and secs >= 0
     assert srv.t[-1] - srv.t[0] < 0.5  # all at once, not paced
+
+
+class _OneAtATimeServer(_FakeServer):
+    """Completes one request per `service` seconds, in submission order,
+    on a worker thread; records how many were in the server at once."""
+
+    def __init__(self, service):
+        super().__init__()
+        import threading
+        self.service, self.pending, self.live, self.max_live = service, queue.Queue(), 0, 0
+        self.lock = threading.Lock()
+        self.submitted = []
+        threading.Thread(target=self._work, daemon=True).start()
+
+    def submit(self, mid, X, to_host=True):
+        r = _FakeRequest(mid, X)
+        with self.lock:
+            self.live += 1
+            self.max_live = max(self.max_live, self.live)
+        self.submitted.append(r)
+        self.pending.put(r)
+        return r
+
+    def _work(self):
+        while True:
+            r = self.pending.get()
+            time.sleep(self.service)
+            with self.lock:
+                self.live -= 1
+            self.q.put(r)
+
+
+def test_closed_loop_keeps_the_window_full_and_measures_the_service_rate():
+    srv = _OneAtATimeServer(0.002)
+    done, secs = serving.closed_loop(srv, 8, 0.5, _make, seed=2)
+    assert srv.max_live <= 8  # never more than the window outstanding
+    assert all(r.released for r in srv.submitted)  # drained and released
+    assert srv.live == 0 and srv.q.empty()
+    rate = done / secs
+    assert 0.5 / 0.002 < rate <= 1.05 / 0.002  # one request per service time, minus sleep overshoot
