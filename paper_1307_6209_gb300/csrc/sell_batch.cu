@@ -113,10 +113,11 @@ __device__ __forceinline__ void batch_unit(const LaunchParams &lp) {
 // Their entry point therefore asks for 6 resident blocks (5 for bfloat16 and
 // for two vectors), which fits them in 40-48 registers with no spills (ptxas
 // -v).  The four-vector variants keep the allocation ptxas picks without a
-// bound (64 registers, 4 blocks per SM).  The eight-vector variants would take
-// 64-76 (3 blocks per SM for binary32); they ask for 4 resident blocks, which
-// caps them at 64 registers with 16-40 bytes of spills and measured 5 %
-// faster on the 512-matrix binary32 batch (1.95 -> 2.04 TF/s, 256 threads).
+// bound (64 registers, 4 blocks per SM; 80 for binary64).  The eight-vector
+// variants would take 64-76 (3 blocks per SM for binary32); they ask for 4
+// resident blocks, which caps them at 64 registers with 12-36 bytes of spills
+// (132 for binary64, measured no slower than 16) and measured 5 % faster on
+// the 512-matrix binary32 batch (1.95 -> 2.04 TF/s, 256 threads).
 template <class VT, int K>
 constexpr int narrow_min_blocks() {
     return K == 1 && !std::is_same<VT, __nv_bfloat16>::value ? 6 : 5;
