@@ -305,7 +305,7 @@ sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s
             P.type = h->store_type;
             P.acc = (it.flags & SELL_SPMV_ACCUMULATE) ? 1 : 0;
             P.comp = h->store_type != SELL_F64 ? comp_mode(it.flags) : 0;
-            P.vec = x_vec(P.X, it.ldx, xs);
+            P.vec = x_vec(P.X, it.ldx, xs) | (x_vec(P.Y, it.ldy, xs) << 2);
             prods.push_back(P);
             owner.push_back(h);
             done += kb;

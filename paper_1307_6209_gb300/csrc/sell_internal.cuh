@@ -82,8 +82,9 @@ inline int rhs_block(int rem, int maxw) {
     return kb;
 }
 
-// How the kernels may load a row of X (base X, row pitch ldx elements of xs
-// bytes): 2 with 32-byte vectors, 1 with 16-byte vectors, 0 value by value.
+// How the kernels may load a row of X, or store a row of Y (base, row pitch
+// ld elements of xs bytes): 2 with 32-byte vectors, 1 with 16-byte vectors,
+// 0 value by value.  The kernels take X's in bits 0-1 and Y's in bits 2-3.
 inline int x_vec(const void *X, int64_t ldx, size_t xs) {
     const uintptr_t a = (uintptr_t)X;
     const int64_t pitch = ldx * (int64_t)xs;

@@ -118,15 +118,16 @@ __device__ __forceinline__ void ld_x32(const double *p, double *v) {
 }
 
 // K consecutive right-hand-side values of row `ci` of X (row-major, ldx).
-// vec: 2 when X and its row pitch are 32-byte aligned (rows of a multiple of
-// 32 bytes then take one 256-bit load per 32 bytes: a random row costs one
-// L1 request instead of two), 1 when they are 16-byte aligned (16-byte
-// vector loads), 0 otherwise (one load per value).  The values loaded are
-// the same in every case.
+// vec & 3: 2 when X and its row pitch are 32-byte aligned (rows of a
+// multiple of 32 bytes then take one 256-bit load per 32 bytes: a random row
+// costs one L1 request instead of two), 1 when they are 16-byte aligned
+// (16-byte vector loads), 0 otherwise (one load per value); bits 2-3 hold the
+// same for Y (store_y).  The values loaded are the same in every case.
 template <int K, class XT>
 __device__ __forceinline__ void load_x(const XT *__restrict__ X, int64_t ldx, int32_t ci, int vec,
                                        XT (&xv)[K]) {
     const XT *p = X + (int64_t)ci * ldx;
+    vec &= 3;
     if constexpr (K == 1) {
         xv[0] = __ldg(p);
     } else {
@@ -156,6 +157,97 @@ __device__ __forceinline__ void load_x(const XT *__restrict__ X, int64_t ldx, in
         } else {
 #pragma unroll
             for (int q = 0; q < K; ++q) xv[q] = __ldg(p + q);
+        }
+    }
+}
+
+// 32 bytes of Y at p (32-byte aligned) in one 256-bit store or load.
+__device__ __forceinline__ void st_y32(float *p, const float *v) {
+    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(v[0]), "f"(v[1]), "f"(v[2]),
+                 "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+                 : "memory");
+}
+__device__ __forceinline__ void st_y32(double *p, const double *v) {
+    asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p), "d"(v[0]), "d"(v[1]), "d"(v[2]), "d"(v[3])
+                 : "memory");
+}
+__device__ __forceinline__ void ld_y32(const float *p, float *v) {
+    asm volatile("ld.global.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+                 : "l"(p)
+                 : "memory");
+}
+__device__ __forceinline__ void ld_y32(const double *p, double *v) {
+    asm volatile("ld.global.v4.f64 {%0,%1,%2,%3}, [%4];"
+                 : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3])
+                 : "l"(p)
+                 : "memory");
+}
+
+// Row i of Y (K values, row-major, ldy) written, or read for accumulation,
+// with the widest vectors that bits 2-3 of vec allow (the layout of load_x).
+// One vector store per 32 bytes instead of K scalar stores: each scalar
+// store of a scattered row is an L2 request of its own.
+template <int K, class XT>
+__device__ __forceinline__ void store_y(XT *Y, int64_t ldy, int64_t i, int vec, const XT (&v)[K]) {
+    XT *p = Y + i * ldy;
+    const int yv = (vec >> 2) & 3;
+    if constexpr (K == 1) {
+        p[0] = v[0];
+    } else {
+        constexpr int V = 16 / sizeof(XT);
+        constexpr int W = 32 / sizeof(XT);
+        if ((K % W) == 0 && yv >= 2) {
+#pragma unroll
+            for (int q = 0; q < K; q += W) st_y32(p + q, v + q);
+        } else if ((K % V) == 0 && yv) {
+            if constexpr (sizeof(XT) == 8) {
+#pragma unroll
+                for (int q = 0; q < K; q += 2) *reinterpret_cast<double2 *>(p + q) = make_double2(v[q], v[q + 1]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < K; q += 4)
+                    *reinterpret_cast<float4 *>(p + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < K; ++q) p[q] = v[q];
+        }
+    }
+}
+template <int K, class XT>
+__device__ __forceinline__ void load_y(const XT *Y, int64_t ldy, int64_t i, int vec, XT (&v)[K]) {
+    const XT *p = Y + i * ldy;
+    const int yv = (vec >> 2) & 3;
+    if constexpr (K == 1) {
+        v[0] = p[0];
+    } else {
+        constexpr int V = 16 / sizeof(XT);
+        constexpr int W = 32 / sizeof(XT);
+        if ((K % W) == 0 && yv >= 2) {
+#pragma unroll
+            for (int q = 0; q < K; q += W) ld_y32(p + q, v + q);
+        } else if ((K % V) == 0 && yv) {
+            if constexpr (sizeof(XT) == 8) {
+#pragma unroll
+                for (int q = 0; q < K; q += 2) {
+                    const double2 t = *reinterpret_cast<const double2 *>(p + q);
+                    v[q] = t.x;
+                    v[q + 1] = t.y;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < K; q += 4) {
+                    const float4 t = *reinterpret_cast<const float4 *>(p + q);
+                    v[q] = t.x;
+                    v[q + 1] = t.y;
+                    v[q + 2] = t.z;
+                    v[q + 3] = t.w;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < K; ++q) v[q] = p[q];
         }
     }
 }
@@ -388,11 +480,20 @@ __device__ __forceinline__ void short_row(const VT *__restrict__ val, const int3
     const int64_t out = perm ? (int64_t)perm[r] : r;
     const int64_t base = cs[c] + l;
     Acc acc[K];
+    if (accumulate) {
+        XT y0[K];
+        load_y<K>(Y, ldy, out, vec, y0);
 #pragma unroll
-    for (int q = 0; q < K; ++q) acc[q].init(accumulate ? Y[out * ldy + q] : XT(0));
+        for (int q = 0; q < K; ++q) acc[q].init(y0[q]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < K; ++q) acc[q].init(XT(0));
+    }
     chain<VT, XT, K, U, PIPE, Acc>(acc, val + base, col + base, C, 0, L, X, ldx, vec, pol);
+    XT yo[K];
 #pragma unroll
-    for (int q = 0; q < K; ++q) Y[out * ldy + q] = acc[q].result();
+    for (int q = 0; q < K; ++q) yo[q] = acc[q].result();
+    store_y<K>(Y, ldy, out, vec, yo);
 }
 
 }  // namespace sell

@@ -58,7 +58,7 @@ sell_status launch_spmmv(sell_matrix *h, const void *X, int64_t ldx, void *Y, in
         const int kb = rhs_block(k - done, maxw);
         const char *Xb = static_cast<const char *>(X) + (size_t)done * xs;
         char *Yb = static_cast<char *>(Y) + (size_t)done * xs;
-        int vec = x_vec(Xb, ldx, xs);
+        int vec = x_vec(Xb, ldx, xs) | (x_vec(Yb, ldy, xs) << 2);
         cudaError_t e = dispatch(h, Xb, ldx, Yb, ldy, kb, acc, vec, comp, nullptr, nullptr, nullptr, s);
         if (e != cudaSuccess) return cuda_fail(e, "SpMV kernel launch");
         done += kb;
@@ -75,7 +75,7 @@ sell_status launch_block_with_scratch(const sell_matrix *h, const void *X, int64
     const int acc = (flags & SELL_SPMV_ACCUMULATE) ? 1 : 0;
     const int comp = comp_mode(flags);
     const size_t xs = h->store_type == SELL_F64 ? 8 : 4;
-    const int vec = x_vec(X, ldx, xs);
+    const int vec = x_vec(X, ldx, xs) | (x_vec(Y, ldy, xs) << 2);
     cudaError_t e = dispatch(h, X, ldx, Y, ldy, kb, acc, vec, comp, part, cnt, cnt2, s);
     if (e != cudaSuccess) return cuda_fail(e, "SpMV kernel launch");
     return SELL_OK;

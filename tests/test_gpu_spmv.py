@@ -350,12 +350,14 @@ def test_spmmv_rhs_block_flags_keep_the_bits(k):
 
 
 @pytest.mark.parametrize("store,k", [("f64", 4), ("f64", 8), ("f32", 8), ("f32", 16)])
-def test_spmmv_x_row_load_widths_keep_the_bits(store, k):
-    """A row of X is loaded 32 bytes at a time when X and its pitch are
-    32-byte aligned, 16 bytes at a time when they are 16-byte aligned, value
-    by value otherwise.  The pitch (ldx = k, k + 16 / size, k + 1) and a
-    shifted base pick each width; every result is the same bits, within the
-    oracle's bound, through the batch plan as well."""
+def test_spmmv_row_vector_widths_keep_the_bits(store, k):
+    """A row of X is loaded, and a row of Y stored (and read back for
+    accumulation), 32 bytes at a time when the base and the pitch are 32-byte
+    aligned, 16 bytes at a time when they are 16-byte aligned, value by value
+    otherwise.  Pitches k, k + 16 / size and k + 1 and a 16-byte shifted base
+    pick each width for X and Y independently; every result is the same bits,
+    within the oracle's bound, with and without accumulation, through the
+    batch plan as well; Y's padding columns stay untouched."""
     import torch
     from paper_1307_6209_gb300 import sell
     from tests.gpu_util import assert_oracle_parity
@@ -366,21 +368,37 @@ def test_spmmv_x_row_load_widths_keep_the_bits(store, k):
     A = synth.lognormal(7000, seed=60 + k, cap=900)
     h = sell.sell_build(A, C=64, sigma=4096, store_type=st)
     X0 = torch.from_numpy(synth.block(A.ncols, k, seed=k)).to(dt)
-    ref = None
-    for ldx, shift in ((k, 0), (k + 16 // es, 0), (k + 1, 0), (k, 16 // es)):
-        buf = torch.full((A.ncols * ldx + shift + 64,), float("nan"), dtype=dt, device="cuda")
-        X = buf[shift:shift + A.ncols * ldx].view(A.ncols, ldx)[:, :k]
-        X.copy_(X0)
-        Y = torch.full((A.nrows, k), float("nan"), dtype=dt, device="cuda")
-        sell.sell_spmmv(h, X, Y)
-        torch.cuda.synchronize()
-        if ref is None:
-            ref = Y.clone()
-            assert_oracle_parity(A, st, X0.numpy(), Y.cpu().numpy(), what=f"{store} k={k}")
-        assert torch.equal(Y, ref), f"ldx {ldx}, base shift {shift}"
-        Yb = torch.full((A.nrows, k), float("nan"), dtype=dt, device="cuda")
-        plan = sell.sell_batch_create([(h, X, Yb, 0)])
-        plan.run()
-        torch.cuda.synchronize()
-        plan.free()
-        assert torch.equal(Yb, ref), f"batch: ldx {ldx}, base shift {shift}"
+    Y0 = torch.from_numpy(synth.block(A.nrows, k, seed=k + 100)).to(dt)
+    layouts = ((k, 0), (k + 16 // es, 0), (k + 1, 0), (k, 16 // es))
+
+    def view(n, ld, shift, fill):
+        buf = torch.full((n * ld + shift + 64,), fill, dtype=dt, device="cuda")
+        return buf, buf[shift:shift + n * ld].view(n, ld)[:, :k]
+
+    ref = {}
+    for acc in (0, sell.SELL_SPMV_ACCUMULATE):
+        for (ldx, sx), (ldy, sy) in zip(layouts, layouts[1:] + layouts[:1]):
+            _, X = view(A.ncols, ldx, sx, float("nan"))
+            X.copy_(X0)
+            for batch in (False, True):
+                ybuf, Y = view(A.nrows, ldy, sy, -7.0)
+                if acc:
+                    Y.copy_(Y0)
+                else:
+                    Y.fill_(float("nan"))
+                if batch:
+                    plan = sell.sell_batch_create([(h, X, Y, acc)])
+                    plan.run()
+                    torch.cuda.synchronize()
+                    plan.free()
+                else:
+                    sell.sell_spmmv(h, X, Y, flags=acc)
+                    torch.cuda.synchronize()
+                if acc not in ref:
+                    ref[acc] = Y.clone()
+                    assert_oracle_parity(A, st, X0.numpy(), Y.cpu().numpy(), flags=acc,
+                                         Y0=Y0.numpy() if acc else None, what=f"{store} k={k} acc={acc}")
+                what = f"acc {acc}, ldx {ldx}+{sx}, ldy {ldy}+{sy}, batch {batch}"
+                assert torch.equal(Y, ref[acc]), what
+                pad = ybuf[sy:sy + A.nrows * ldy].view(A.nrows, ldy)[:, k:]
+                assert bool((pad == -7.0).all()), what + ": padding columns written"
