@@ -367,8 +367,10 @@ SELL_API sell_status sell_batch_free(sell_batch_plan plan);
  * others run are admitted as soon as a stream and memory are free, and their
  * work overlaps on the device.  The inputs of all batches go through one
  * copy stream of the server's in 4 MB pieces, the batch with the fewest bytes
- * left first, so a small request's input does not wait for a large one's;
- * a batch's kernels start once its inputs are issued.  A batch whose requests
+ * left first -- a waiting batch's count falling by 200 GB per second of its
+ * age, so that a large input is not starved by a stream of small ones -- so a
+ * small request's input waits for at most one aged large input rather than
+ * for every large one; a batch's kernels start once its inputs are issued.  A batch whose requests
  * differ widely in size runs in two parts, the small requests (work at most
  * 1/8 of its largest) first with their own completion.  Every result is
  * bitwise the result of the same product alone. */

@@ -14,9 +14,13 @@
 //     copy issued after a 256 MB one on another stream finishes with it,
 //     1.3 ms later), so every input goes through one copy stream in chunks
 //     of kChunk bytes, at most kWindow bytes in flight, the batch with the
-//     fewest bytes left first; a batch's kernels are enqueued behind an event
+//     fewest bytes left first, where a waiting batch's count falls at
+//     kAgeRate bytes per second of its age (a large input is not starved by
+//     a stream of small ones: it waits about its own copy time at most
+//     before it goes first); a batch's kernels are enqueued behind an event
 //     recorded after its last chunk.  A small request then waits for at
-//     most a window of chunks instead of a large request's whole input;
+//     most a window of chunks, or one aged large input, instead of every
+//     large input issued before it;
 //   * runs a batch in two parts when its products differ widely in size:
 //     the requests whose work is at most 1/kPartRatio of the batch's largest
 //     go first, with their own input copies, plan and completion event, so
@@ -71,6 +75,12 @@ struct Req {
 // kWindow bytes in flight on the copy stream (about 160 us at 200 GB/s).
 constexpr size_t kChunk = 4u << 20;
 constexpr size_t kWindow = 32u << 20;
+// The copy order's aging: a part's bytes left, less its age times this rate
+// (about the copy engine's host-to-device rate), picks the next chunk.
+// Plain fewest-bytes-left-first starved large inputs: under Poisson load
+// parts of 0.25-1 GB waited 50-170 ms for their chunks to be issued (then
+// copied in a few ms) while smaller parts kept arriving.
+constexpr double kAgeRate = 200e9;
 
 struct Chunk {
     char *dst;
@@ -92,6 +102,7 @@ struct Part {
     bool launched = false;      // kernels, result copies and completion event enqueued
     bool retired = false;       // its requests are done
     sell_status status = SELL_OK;
+    double t_admit = 0;         // when its batch was admitted (the copy order's age)
 };
 
 // A batch holds one stream; its parts run on it in order (part 0 first).
@@ -213,6 +224,7 @@ void prepare(sell_server *S, int si, std::vector<Req *> &batch, Batch &B) {
         r->batch = n;
         const int p = (B.nparts == 2 && work(S, r) * kPartRatio > wmax) ? 1 : 0;
         Part &P = B.parts[p];
+        P.t_admit = t;
         P.reqs.push_back(r);
         auto add = [&](char *dst, const void *src, size_t bytes) {
             const char *s = static_cast<const char *>(src);
@@ -278,7 +290,7 @@ void finish_launch(sell_server *S, Batch &B, int p) {
 // retire the chunks that have landed, launch the parts whose copies are all
 // issued (a batch's second part after its first), and issue further chunks
 // while the window has room -- always from the part with the fewest bytes
-// left (the earliest admitted on ties).
+// left less kAgeRate times its age (the earliest admitted on ties).
 void pump(sell_server *S) {
     while (!S->copying.empty()) {
         const cudaError_t q = cudaEventQuery(S->copying.front().first);
@@ -288,8 +300,10 @@ void pump(sell_server *S) {
         S->spare.push_back(S->copying.front().first);
         S->copying.pop_front();
     }
+    const double now = now_s();
     for (;;) {
         Part *pick = nullptr;
+        double best = 0;
         for (Batch &B : S->inflight) {
             for (int p = 0; p < B.nparts; ++p) {
                 Part &P = B.parts[p];
@@ -299,7 +313,11 @@ void pump(sell_server *S) {
                     finish_launch(S, B, p);
                     continue;
                 }
-                if (!pick || P.left < pick->left) pick = &P;
+                const double key = (double)P.left - (now - P.t_admit) * kAgeRate;
+                if (!pick || key < best) {
+                    pick = &P;
+                    best = key;
+                }
             }
         }
         if (!pick || S->copy_bytes >= kWindow) return;
