@@ -67,17 +67,20 @@ struct LaunchParams {
 };
 
 // One block per work unit, long-row units first in the grid so that they
-// start early (the same shape as the single-product kernel).  The one- and
-// two-vector variants issue the next group's val/col loads before the
-// current group's gathers (software pipelining, as launch mode 1 of the
-// single product; the FMA order and so the bits are unchanged): measured
-// 3 % faster on a 256-matrix banded binary32 batch and 2 % on the
-// 512-matrix mixed one.
+// start early (the same shape as the single-product kernel).  Every variant
+// issues the next group's val/col loads before the current group's gathers
+// (software pipelining, as launch mode 1 of the single product; the FMA
+// order and so the bits are unchanged).  Measured on 256-matrix binary32
+// batches: banded k = 1 3 % faster (the 512-matrix mixed one 2 %); at k = 8
+// banded 2.16 -> 1.79 ms and lognormal 2.45 -> 2.15 ms, at k = 4 banded
+// 1.84 -> 1.67 ms and lognormal unchanged -- without it the wide variants,
+// at 64 registers and half the SM's warps, kept too few stream bytes in
+// flight.
 template <class VT, int K, class Acc, class AccL, bool LONG = true>
 __device__ __forceinline__ void batch_unit(const LaunchParams &lp) {
     using XT = typename XType<VT>::T;
     constexpr int U = K >= 4 ? 2 : 4;
-    constexpr bool PIPE = K <= 2;
+    constexpr bool PIPE = true;
     const uint64_t pol = l2_evict_first_policy();
     const int32_t w = (int32_t)blockIdx.x;
     if (w >= lp.start[2 * lp.nprod]) return;
