@@ -153,14 +153,11 @@ cudaError_t pick_u(const sell_matrix *h, const void *X, int64_t ldx, void *Y, in
     }
 }
 
-// The software-pipelined chain is built for 1 and 2 right-hand sides (wider
-// blocks already keep many loads in flight and would double their registers).
+// Launch mode 1 runs the software-pipelined chain at every block width.
 template <class VT, int K, class Acc, class AccL>
 cudaError_t pick_unroll(const sell_matrix *h, const void *X, int64_t ldx, void *Y, int64_t ldy,
                         int acc, int vec, cudaStream_t s) {
-    if constexpr (K <= 2) {
-        if (h->pipeline == 1) return pick_u<VT, K, true, Acc, AccL>(h, X, ldx, Y, ldy, acc, vec, s);
-    }
+    if (h->pipeline == 1) return pick_u<VT, K, true, Acc, AccL>(h, X, ldx, Y, ldy, acc, vec, s);
     return pick_u<VT, K, false, Acc, AccL>(h, X, ldx, Y, ldy, acc, vec, s);
 }
 
