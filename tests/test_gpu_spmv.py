@@ -402,3 +402,33 @@ def test_spmmv_row_vector_widths_keep_the_bits(store, k):
                 assert torch.equal(Y, ref[acc]), what
                 pad = ybuf[sy:sy + A.nrows * ldy].view(A.nrows, ldy)[:, k:]
                 assert bool((pad == -7.0).all()), what + ": padding columns written"
+
+
+@pytest.mark.parametrize("store,comp", [("f64", 0), ("f32", 0), ("f32", 2), ("bf16", 1)])
+@pytest.mark.parametrize("k", [4, 8, 12])
+def test_spmmv_launch_modes_keep_the_bits(store, comp, k):
+    """Launch modes 0 (per-thread loads) and 1 (software-pipelined, at every
+    block width of right-hand sides) and every unroll multiply k right-hand
+    sides to the same bits, on a matrix with long rows (the segment path) and
+    one without; the first result is checked against the oracle."""
+    import torch
+    from paper_1307_6209_gb300 import sell
+    from tests.gpu_util import assert_oracle_parity
+
+    st = {"f64": sell.SELL_F64, "f32": sell.SELL_F32, "bf16": sell.SELL_BF16}[store]
+    fl = [0, sell.SELL_SPMV_COMPENSATED, sell.SELL_SPMV_COMPENSATED_LONG][comp]
+    dt = torch.float64 if store == "f64" else torch.float32
+    for A in (synth.lognormal(6000, seed=70 + k, cap=1500), synth.banded(7000, seed=71 + k)):
+        h = sell.sell_build(A, C=64, sigma=512, store_type=st)
+        X0 = torch.from_numpy(synth.block(A.ncols, k, seed=k)).to(dt)
+        X = X0.cuda()
+        ref = None
+        for block, unroll, mode in ((128, 1, 0), (128, 2, 1), (256, 4, 1), (128, 1, 1), (512, 8, 1), (128, 4, 0)):
+            sell.sell_set_launch(h, block, unroll, mode)
+            Y = torch.full((A.nrows, k), float("nan"), dtype=dt, device="cuda")
+            sell.sell_spmmv(h, X, Y, flags=fl)
+            torch.cuda.synchronize()
+            if ref is None:
+                ref = Y.clone()
+                assert_oracle_parity(A, st, X0.numpy(), Y.cpu().numpy(), flags=fl, what=f"{store} k={k}")
+            assert torch.equal(Y, ref), f"block {block} unroll {unroll} mode {mode}"
