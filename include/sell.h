@@ -256,14 +256,16 @@ SELL_API sell_status sell_spmmv_noalloc(sell_handle h, const void *X, int64_t ld
  *   pipeline how the matrix stream (val/col) is read; -1 keeps it:
  *            0 every thread loads its own entries;
  *            1 as 0, with the next step's loads issued before the current
- *              step's gathers (software pipelining; 1 and 2 right-hand sides);
+ *              step's gathers (software pipelining, at every number of
+ *              right-hand sides);
  *            2 bulk-staged: each warp copies whole pieces of its chunks into
  *              shared memory with asynchronous bulk copies while it multiplies
  *              the previous piece (single right-hand sides; C = 32, 64 or 128;
  *              block = warps per block x 32, unroll 1/2/4/8 = 1/2/3/4 pieces
- *              per warp; with 1 the next copy starts when the piece is used).  Selecting it computes the per-warp work
- *              split of the handle on the device (synchronous; a few small
- *              allocations through the handle's allocator).
+ *              per warp; with 1 the next copy starts when the piece is used).
+ *              Selecting it computes the per-warp work split of the handle on
+ *              the device (synchronous; a few small allocations through the
+ *              handle's allocator).
  * Errors: SELL_EINVAL (values), SELL_EUNSUPPORTED (pipeline 2 with another
  * C, or a block that does not fit on an SM), SELL_ENOMEM, SELL_ECUDA. */
 SELL_API sell_status sell_set_launch(sell_handle h, int32_t block, int32_t unroll, int32_t pipeline);
