@@ -432,7 +432,7 @@ __device__ __forceinline__ void long_unit(const VT *__restrict__ val, const int3
     for (int q = 0; q < K; ++q) acc[q].init((s == 0 && accumulate) ? Y[out * ldy + q] : XT(0));
     const int64_t base = cs[c] + l;
     chain<VT, XT, K, U, PIPE, Acc>(acc, val + base, col + base, C, s * kSeg, min(L, (s + 1) * kSeg), X, ldx,
-                                   vec, pol);
+                                   vec & 3, pol);
     using PT = typename PartOf<Acc>::T;
     PT *pp = reinterpret_cast<PT *>(part);
 #pragma unroll
@@ -489,7 +489,7 @@ __device__ __forceinline__ void short_row(const VT *__restrict__ val, const int3
 #pragma unroll
         for (int q = 0; q < K; ++q) acc[q].init(XT(0));
     }
-    chain<VT, XT, K, U, PIPE, Acc>(acc, val + base, col + base, C, 0, L, X, ldx, vec, pol);
+    chain<VT, XT, K, U, PIPE, Acc>(acc, val + base, col + base, C, 0, L, X, ldx, vec & 3, pol);
     XT yo[K];
 #pragma unroll
     for (int q = 0; q < K; ++q) yo[q] = acc[q].result();
