@@ -155,6 +155,22 @@ __global__ void __launch_bounds__(kTileRows, 8) k_batch_short(const __grid_const
     batch_unit<VT, 1, Acc, Acc, true>(lp);
 }
 
+// The same for four and eight right-hand sides of binary32 and bfloat16
+// storage: 6 and 5 resident blocks (40 and 48 registers) instead of the 4
+// of the general variants.  (Binary64 rows of four and eight values do not
+// fit: ptxas spills 208 and 856 bytes there, so those keep the general
+// variants.)
+template <int K>
+constexpr int short_min_blocks() {
+    return K == 4 ? 6 : 5;
+}
+
+template <class VT, int K, class Acc>
+__global__ void __launch_bounds__(kTileRows, (short_min_blocks<K>()))
+k_batch_short_wide(const __grid_constant__ LaunchParams lp) {
+    batch_unit<VT, K, Acc, Acc, true>(lp);
+}
+
 using KernelFn = void (*)(const LaunchParams);
 
 template <class VT, class Acc, class AccL = Acc>
@@ -175,12 +191,22 @@ KernelFn kernel_for_reduced(int comp, int kb) {
     return kernel_for_k<VT, Plain<float>>(kb);
 }
 
-// The entry point of products without long rows at one right-hand side
-// (Dot2 on long rows only is then plain accumulation: there is no long row).
-KernelFn kernel_for_short(int type, int comp) {
-    if (type == SELL_F64) return k_batch_short<double, Plain<double>>;
-    if (type == SELL_F32) return comp == 1 ? k_batch_short<float, Dot2> : k_batch_short<float, Plain<float>>;
-    return comp == 1 ? k_batch_short<__nv_bfloat16, Dot2> : k_batch_short<__nv_bfloat16, Plain<float>>;
+template <class VT, class Acc>
+KernelFn short_for_k(int kb) {
+    switch (kb) {
+        case 1: return k_batch_short<VT, Acc>;
+        case 4: return k_batch_short_wide<VT, 4, Acc>;
+        default: return k_batch_short_wide<VT, 8, Acc>;
+    }
+}
+
+// The entry point of products without long rows at 1, 4 or 8 right-hand
+// sides (Dot2 on long rows only is then plain accumulation: there is no long
+// row).
+KernelFn kernel_for_short(int type, int comp, int kb) {
+    if (type == SELL_F64) return k_batch_short<double, Plain<double>>;  // kb == 1 only
+    if (type == SELL_F32) return comp == 1 ? short_for_k<float, Dot2>(kb) : short_for_k<float, Plain<float>>(kb);
+    return comp == 1 ? short_for_k<__nv_bfloat16, Dot2>(kb) : short_for_k<__nv_bfloat16, Plain<float>>(kb);
 }
 
 KernelFn kernel_for(int type, int comp, int kb) {
@@ -314,13 +340,14 @@ sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s
             done += kb;
         }
     }
-    // group by kernel variant (one-vector products without long rows apart:
-    // their entry point has no long-row path); inside a group: long-row work
-    // first, biggest first
+    // group by kernel variant (products without long rows at 1, 4 or 8
+    // right-hand sides apart: their entry points hold fewer registers);
+    // inside a group: long-row work first, biggest first
     std::map<std::tuple<int, int, int, int>, std::vector<int32_t>> groups;
     for (size_t i = 0; i < prods.size(); ++i) {
         const Prod &P = prods[i];
-        const int short_only = (P.kb == 1 && P.long_threads == 0) ? 1 : 0;
+        const int short_only =
+            (P.long_threads == 0 && (P.kb == 1 || (P.kb >= 4 && P.type != SELL_F64))) ? 1 : 0;
         groups[std::make_tuple(P.type, P.comp, P.kb, short_only)].push_back((int32_t)i);
     }
     int dev = 0;
@@ -347,7 +374,8 @@ sell_status batch_create(const sell_batch_item *items, int32_t n, cudaStream_t s
     for (auto &o : order) {
         const int g = o.second;
         // launches of at most kLaunchProds products each
-        KernelFn fn = std::get<3>(gkey[g]) ? kernel_for_short(std::get<0>(gkey[g]), std::get<1>(gkey[g]))
+        KernelFn fn = std::get<3>(gkey[g]) ? kernel_for_short(std::get<0>(gkey[g]), std::get<1>(gkey[g]),
+                                                              std::get<2>(gkey[g]))
                                            : kernel_for(std::get<0>(gkey[g]), std::get<1>(gkey[g]), std::get<2>(gkey[g]));
         const std::vector<int32_t> &ids = gids[g];
         for (size_t p0 = 0; p0 < ids.size(); p0 += kLaunchProds) {
