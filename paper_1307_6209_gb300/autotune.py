@@ -5,8 +5,8 @@ The paper leaves the choice of sigma and of the threads per row to future
 work (Sec. 6) and notes that the best sigma is matrix dependent (Sec. 3.4,
 Sec. 5.3).  Stage 1 builds every (C, sigma) candidate and times the SpMV with
 the default launch; stage 2 sweeps (block, unroll, pipeline) on the best
-formats (software pipelining for 1 and 2 right-hand sides, bulk staging for
-single right-hand sides, where they exist).  All
+formats (software pipelining at every number of right-hand sides, bulk
+staging for single right-hand sides, where they exist).  All
 timing goes through the C ABI (CUDA events on the given stream).  Results are
 cached in a JSON file keyed by a matrix signature (sizes, longest row, the
 coefficient of variation of Eq. "cv", storage type, right-hand sides).
