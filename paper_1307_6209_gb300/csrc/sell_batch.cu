@@ -115,8 +115,10 @@ __device__ __forceinline__ void batch_unit(const LaunchParams &lp) {
 // sake of the long-row path, although the short rows carry most of the work.
 // Their entry point therefore asks for 6 resident blocks (5 for bfloat16 and
 // for two vectors), which fits them in 40-48 registers with no spills (ptxas
-// -v).  The four-vector variants keep the allocation ptxas picks without a
-// bound (64 registers, 4 blocks per SM; 80 for binary64).  The eight-vector
+// -v).  The four-vector variants ask for 5 blocks (48 registers; binary32
+// without spills): measured against ptxas's own 64 registers (4 blocks) on
+// 256 lognormal binary32 matrices 2.17 -> 1.90 ms and on the 512-matrix
+// mixed batch 7.00 -> 5.01 ms; binary64 unchanged.  The eight-vector
 // variants would take 64-76 (3 blocks per SM for binary32); they ask for 4
 // resident blocks, which caps them at 64 registers with 12-36 bytes of spills
 // (132 for binary64, measured no slower than 16) and measured 5 % faster on
@@ -133,7 +135,7 @@ k_batch_narrow(const __grid_constant__ LaunchParams lp) {
 }
 
 template <class VT, int K, class Acc, class AccL = Acc>
-__global__ void __launch_bounds__(kTileRows) k_batch(const __grid_constant__ LaunchParams lp) {
+__global__ void __launch_bounds__(kTileRows, 5) k_batch(const __grid_constant__ LaunchParams lp) {
     batch_unit<VT, K, Acc, AccL>(lp);
 }
 
