@@ -119,10 +119,12 @@ __device__ __forceinline__ void batch_unit(const LaunchParams &lp) {
 // without spills): measured against ptxas's own 64 registers (4 blocks) on
 // 256 lognormal binary32 matrices 2.17 -> 1.90 ms and on the 512-matrix
 // mixed batch 7.00 -> 5.01 ms; binary64 unchanged.  The eight-vector
-// variants would take 64-76 (3 blocks per SM for binary32); they ask for 4
-// resident blocks, which caps them at 64 registers with 12-36 bytes of spills
-// (132 for binary64, measured no slower than 16) and measured 5 % faster on
-// the 512-matrix binary32 batch (1.95 -> 2.04 TF/s, 256 threads).
+// variants would take 64-76 (3 blocks per SM for binary32).  4 resident
+// blocks (64 registers) measured 5 % faster than that on the 512-matrix
+// binary32 batch; binary32 and bfloat16 now ask for 5 (48 registers, 92
+// bytes of spills): 256 lognormal binary32 matrices 2.17 -> 2.12 ms, a
+// 512-matrix mixed batch 6.28 -> 5.55 ms.  Binary64 keeps 4 (5 measured 6 %
+// slower).
 template <class VT, int K>
 constexpr int narrow_min_blocks() {
     return K == 1 && !std::is_same<VT, __nv_bfloat16>::value ? 6 : 5;
@@ -139,8 +141,14 @@ __global__ void __launch_bounds__(kTileRows, 5) k_batch(const __grid_constant__ 
     batch_unit<VT, K, Acc, AccL>(lp);
 }
 
+template <class VT>
+constexpr int wide_min_blocks() {
+    return sizeof(VT) == 8 ? 4 : 5;
+}
+
 template <class VT, int K, class Acc, class AccL = Acc>
-__global__ void __launch_bounds__(kTileRows, 4) k_batch_wide(const __grid_constant__ LaunchParams lp) {
+__global__ void __launch_bounds__(kTileRows, (wide_min_blocks<VT>()))
+k_batch_wide(const __grid_constant__ LaunchParams lp) {
     batch_unit<VT, K, Acc, AccL>(lp);
 }
 
